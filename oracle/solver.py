@@ -1,0 +1,30 @@
+"""Two-stage approximate inverse of the discrete FIO (Algorithm 1, Eq. 4.1-4.3).
+
+Test infrastructure only: nothing on the product path imports this module.
+
+Offline: BF K~ of K (Section 2.2); black-box HSS G~ of G = K^* K sampled
+through K~^* K~ (Section 3, Section 4.1); ULV factorization F~ of G~
+(Section 2.4).  Online: f^ = F~ K~^* u (Eq. 4.2, direct solver on the
+approximate normal equation Eq. 4.3).
+"""
+import numpy as np
+
+from .butterfly import Butterfly1D
+from .hss import ULV, build_blackbox
+
+
+class FIOSolver:
+    def __init__(self, phase, n, r, leaf, p, tol, seed, rank_frac=0.5):
+        self.bf = Butterfly1D(phase, n, r)
+        self.stats = {}
+        self.hss = build_blackbox(lambda X: self.bf.adjoint(self.bf.apply(X)),
+                                  n, leaf, p, tol, seed, rank_frac=rank_frac, stats=self.stats)
+        self.ulv = ULV(self.hss)
+
+    def solve(self, u):
+        """f^ = F~ (K~^* u)."""
+        return self.ulv.solve(self.bf.adjoint(u))
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
