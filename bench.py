@@ -1,0 +1,355 @@
+"""Benchmark: RHS solves/s of the online stage f = G~^{-1} K~^* u at N = 2^16.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--k 64]
+
+One step = one pass of the online hot path (BF adjoint K~^* + ULV solve of G~)
+over one block of k = 64 right-hand sides (the coalesced "served" block) of
+the 1D operator Phi = x xi + c(x)|xi|, c = (2 + sin 2 pi x)/16, N = 2^16,
+BF rank 16, HSS leaf 128, oversampling 10, HSS tol 1e-3, complex64.  The
+offline stage (bf_build, black-box HSS, ULV factor) runs once before timing
+and its times are reported in `config`.  The plain path (one RHS per call)
+is measured the same way and reported beside it with p50/p99 latencies.
+
+`--impl reference` times the CPU FP64 oracle's online stage on the same
+workload (each step one RHS: K~^* apply with the oracle's factor blocks built
+beforehand, plus the oracle ULV solve on an HSS of the same tree shape).
+Multi-GPU: one process per GPU (torchrun); every rank builds its own replica
+of the operators and solves its own blocks (weak scaling, no collective on the
+data path); rank 0 prints the line with the max time over ranks.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from fio_inputs import WORKLOADS, crandn  # noqa: E402
+
+METRIC = "RHS solves/s at N=2^16 (Kt^* + HSS ULV) vs plain FP32 path; p50/p99 latency"
+UNIT = "RHS/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def kernel_bytes(name, N, r, kc, binfo, hinfo):
+    """Algorithmic HBM bytes of one launch (reads of inputs and tables, writes of outputs)."""
+    S = N * r * kc * 8
+    vec = N * kc * 8
+    tables_quad = 2 * N * r * 8
+    lsU = 1 << (binfo["L"] - binfo["sU"])
+    nVP = (1 << binfo["sV"]) * N * 8
+    if name == "k_U_adj" or name == "k_U_fwd":
+        return vec + N * lsU * 8 + S
+    if name == "k_V_adj" or name == "k_V_fwd":
+        return S + nVP + vec
+    if name.startswith("k_quad"):
+        return 2 * S + tables_quad
+    if name.startswith("k_M"):
+        return 2 * S + N * r * r * 8
+    if name in ("k_ulv_up", "k_ulv_down"):
+        # average over the Lh launches of one pass: W_l plus the level's vectors
+        Lh, leaf, ranks = hinfo["Lh"], hinfo["leaf"], hinfo["ranks"]
+        tot = 0
+        for l in range(1, Lh + 1):
+            m = leaf if l == Lh else 2 * ranks[l + 1]
+            tot += (2 ** l) * m * m * 8 + 2 * (2 ** l) * m * kc * 8
+        return tot / Lh
+    return None
+
+
+def parse_profile(text):
+    out = {}
+    for line in text.strip().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def cpu_oracle_online(n, steps, warmup, leaf, r, rank_per_level=8, seed=3):
+    """Oracle online stage, one RHS per step: K~^* u (factor blocks built first) + ULV solve."""
+    from oracle.butterfly import Butterfly1D
+    from oracle.hss import ULV, random_hss
+    from oracle.problem import Phase
+    cores = len(os.sched_getaffinity(0))
+    bf = Butterfly1D(Phase("cabs"), n, r, cache=True)
+    Lh = int(np.log2(n // leaf))
+    ranks = [0] + [rank_per_level] * Lh
+    hss = random_hss(n, leaf, ranks, np.random.default_rng(0), shift=float(n))
+    ulv = ULV(hss)
+    u = crandn(n, 1, seed)
+    t0 = time.perf_counter()
+    bf.adjoint(u)                      # builds and keeps the factor blocks (offline part)
+    setup = time.perf_counter() - t0
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        ulv.solve(bf.adjoint(crandn(n, 1, seed + 1 + i)))
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+    med = statistics.median(times)
+    sample = (f"{steps} RHS of the N=2^16 workload, one per step (median {med:.2f} s): oracle K~^* apply "
+              f"(complex128, factor blocks built once beforehand in {setup:.1f} s, excluded) + oracle ULV "
+              f"solve on an HSS of the same tree (leaf {leaf}, {Lh} levels, rank {rank_per_level} per level)")
+    return 1.0 / med, cores, sample, times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS["large1d"]
+    value, cores, sample, times = cpu_oracle_online(w["n"], args.steps, args.warmup, w["leaf"], w["r"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "large1d: d=1 N=2^16 Phi=x*xi+c(x)|xi| BF r=16 HSS leaf 128 tol 1e-3, 1 RHS/step",
+                   "k_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    from paper_2609_11520_b300 import _lib
+
+    w = WORKLOADS["large1d"]
+    n, r, k = w["n"], w["r"], args.k
+    stream = torch.cuda.current_stream()
+
+    # ---- offline stage (not timed in `value`) ----
+    t0 = time.perf_counter()
+    bf = BF(n, r, w["phase"], w["s"])
+    t_bf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hss = HSS.from_samples(bf=bf, leaf=w["leaf"], oversample=w["p"], tol=w["tol"], seed=w["seed_omega"] + rank)
+    t_hss = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hss.factor()
+    t_fac = time.perf_counter() - t0
+    binfo, hinfo = bf.info(), hss.info()
+
+    # ---- inputs resident in HBM: u = K~ f_true ----
+    f_true = crandn(n, k, seed=w["seed_f"] + 100 * rank)
+    F_true = torch.from_numpy(np.ascontiguousarray(f_true.T.astype(np.complex64))).cuda()
+    U = bf.apply(F_true)
+    OUT = torch.empty_like(U)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)                       # L2 flush between timed iterations
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    # ---- served path: one coalesced block of k RHS per step ----
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        served = timed(lambda: fio_solve(bf, hss, U, out=OUT), args.steps, args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    tot_ms = sum(served)
+    if world > 1:
+        tt = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    value = world * k * args.steps / (tot_ms / 1e3)
+    e_direct = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+
+    # ---- plain path: one RHS per call ----
+    U1 = U[:1].clone()
+    O1 = torch.empty_like(U1)
+    plain = timed(lambda: fio_solve(bf, hss, U1, out=O1), args.steps, args.warmup)
+    plain_value = 1e3 / statistics.mean(plain)
+
+    # ---- end to end through the public API with pinned host buffers ----
+    Uh = U.cpu().pin_memory()
+    Oh = torch.empty(Uh.shape, dtype=Uh.dtype).pin_memory()
+    Ud = torch.empty_like(U)
+
+    def e2e_step():
+        Ud.copy_(Uh, non_blocking=True)
+        fio_solve(bf, hss, Ud, out=OUT)
+        Oh.copy_(OUT, non_blocking=True)
+
+    e2e = timed(e2e_step, args.steps, args.warmup)
+    e2e_value = world * k * args.steps / (sum(e2e) / 1e3)
+
+    # ---- per-kernel CUDA-event attribution over an identical pass ----
+    _lib.lib.fio_profile_enable(1)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        fio_solve(bf, hss, U, out=OUT)
+    torch.cuda.synchronize()
+    buf = ctypes.create_string_buffer(1 << 16)
+    _lib.check(_lib.lib.fio_profile_report(buf, len(buf)))
+    _lib.lib.fio_profile_enable(0)
+    prof = parse_profile(buf.value.decode())
+    launches = sum(c for c, _ in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kc = min(k, 64)
+    peak, peak_src = load_peaks()
+    per_launch_ms = top[1][1] / top[1][0]
+    nbytes = kernel_bytes(top[0], n, r, kc, binfo, hinfo)
+    achieved = nbytes / (per_launch_ms / 1e3) / 1e9 if nbytes else None
+    kernels = {name: {"launches": c, "ms_total": round(ms, 4), "share": round(ms / sum(v[1] for v in prof.values()), 4)}
+               for name, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, cores, sample, _ = cpu_oracle_online(n, 3, 0, w["leaf"], r)
+        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(served), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {
+                "workload": "large1d: d=1, N=2^16, Phi=x*xi+c(x)|xi|, c=(2+sin 2pi x)/16, a=1, BF r=16, "
+                            "HSS leaf 128, oversample 10, tol 1e-3; served block of k RHS per step",
+                "k_per_step": k, "l2": "flushed between timed steps (256 MiB write)",
+                "offline_s": {"bf_build": round(t_bf, 3), "hss_build": round(t_hss, 3), "ulv_factor": round(t_fac, 3)},
+                "hss_ranks": hinfo["ranks"], "hss_samples": hinfo["samples"],
+                "e_direct_vs_f_true": e_direct, "parallelism": f"replicas x{world}",
+            },
+            "latency_ms": {"served_p50": percentile(served, 50), "served_p99": percentile(served, 99),
+                           "plain_p50": percentile(plain, 50), "plain_p99": percentile(plain, 99)},
+            "plain": {"value": plain_value, "unit": UNIT, "k_per_call": 1},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(U.numel() * 8),
+                    "d2h_bytes_per_step": int(U.numel() * 8)},
+            "gpu_launches": int(launches),
+            "kernels": kernels,
+            "roofline": {"kernel": top[0], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
+                         "bytes_per_launch": nbytes, "traffic": None},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * fio.h -- C ABI of the B300 library for the two-stage approximate inverse of
+ * discrete Fourier integral operators (Li & Liu, "Approximate Inversion of
+ * Discrete Fourier Integral Operators via Hierarchically Semiseparable
+ * Matrices").
+ *
+ * Problem (Eq. 1.1-1.2): K_ij = a(x_i, xi_j) exp(2 pi i Phi(x_i, xi_j)),
+ * x_i = i/n, xi_j = j - n/2 (d = 1), N = n^d, amplitude a = 1.
+ * Offline (Algorithm 1): butterfly factorization K~ of K (Section 2.2,
+ * Eq. 2.1); randomized black-box HSS approximation G~ of G = K^* K sampled
+ * through K~^* K~ (Section 3); ULV factorization of G~ (Section 2.4).
+ * Online (Eq. 4.2): f = G~^{-1} K~^* u.
+ *
+ * Conventions shared by every call:
+ *  - Vectors are complex64 (interleaved float re, im), column-major blocks of
+ *    k columns with leading dimension ld >= N (in complex elements), in
+ *    natural index order: entry j of a frequency-side vector is xi_j = j - n/2,
+ *    entry i of a space-side vector is x_i = i/n.
+ *  - Pointers named "device" must be CUDA device memory on the current
+ *    device; the caller owns them and the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream ordered and return before the GPU work finishes, except
+ *    where a call says it synchronizes.  Asynchronous CUDA errors surface as
+ *    FIO_ECUDA at a later call.
+ *  - Handles (fio_bf, fio_hss) are owned by the library; free them with
+ *    bf_free / hss_free.  A handle may be used by one stream at a time.
+ *  - Every call returns a status; on failure fio_last_error() gives a
+ *    message (thread local).  No call aborts the process.
+ */
+#ifndef FIO_H
+#define FIO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FIO_OK = 0,
+    FIO_EINVAL = 1,    /* bad argument (size, rank, pointer, layout) */
+    FIO_ENOMEM = 2,    /* device allocation failed */
+    FIO_ECUDA = 3,     /* CUDA runtime error (message in fio_last_error) */
+    FIO_ENOTHPD = 4,   /* Cholesky pivot <= 0: G~ is not Hermitian positive definite */
+    FIO_ERANK = 5,     /* HSS rank saturated the sample count */
+    FIO_ETIMEOUT = 6,  /* a bounded device-side wait expired */
+    FIO_EBUSY = 7      /* handle in use */
+} fio_status;
+
+typedef enum {
+    FIO_PHASE_DFT = 0,        /* Phi = x . xi  (then K^* K = N I exactly) */
+    FIO_PHASE_1D_CABS = 1     /* Phi = x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/16 */
+} fio_phase_kind;
+
+typedef struct {
+    int kind;     /* fio_phase_kind */
+    double s;     /* modulation depth s of c(x); 1.0 for the standard operator */
+} fio_phase;
+
+typedef struct fio_bf fio_bf;
+typedef struct fio_hss fio_hss;
+
+/* Sampler for the black-box HSS construction (Section 3): the matrix H whose
+ * products H X the construction may request. */
+typedef enum {
+    FIO_SAMPLER_NORMAL = 0,   /* H = K~^* K~ through `bf` (Section 4.1) */
+    FIO_SAMPLER_DENSE = 1     /* H = dense device matrix (N x N complex64,
+                                 column-major, leading dimension `ld`); for tests */
+} fio_sampler_kind;
+
+typedef struct {
+    int kind;              /* fio_sampler_kind */
+    const fio_bf* bf;      /* FIO_SAMPLER_NORMAL */
+    const void* dense;     /* FIO_SAMPLER_DENSE: device pointer */
+    int64_t ld;            /* FIO_SAMPLER_DENSE: leading dimension (>= N) */
+} fio_sampler;
+
+/* ------------------------------------------------------------------------
+ * bf_build -- butterfly factorization K~ of K (Section 2.2, Eq. 2.1).
+ *   n: points per dimension (power of two, 16 <= n <= 2^24); d: dimension
+ *   (1); r: Chebyshev interpolation rank (1..32).  Trees: space/frequency
+ *   dyadic trees of depth L = log2 n; middle level h = floor(L/2); outermost
+ *   factors at max(L-3, h) (practical top level, Section 5.2).
+ *   Every factor entry is evaluated on the device from its definition
+ *   (phase differences in FP64, reduced mod 1, stored complex64).
+ *   Synchronizes `stream` before returning.  *out receives the handle.
+ *   Errors: FIO_EINVAL (sizes), FIO_ENOMEM, FIO_ECUDA.
+ * ---------------------------------------------------------------------- */
+fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, fio_bf** out);
+
+/* bf_apply -- Y = K~ X (adjoint = 0) or Y = K~^* X (adjoint = 1); the adjoint
+ *   applies the conjugate-transposed factors in reverse order (Section 2.2).
+ *   X, Y: device, N x k complex64, column-major, leading dimension ld >= N;
+ *   X and Y must not overlap.  k >= 0 (k = 0 is a no-op).  Uses the handle's
+ *   scratch state (allocated on first use, grown as needed).
+ *   Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA. */
+fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream);
+
+/* bf_info -- sizes of a handle: out[0..7] = n, d, r, L, h, sU (space level of
+ *   U), sV (space level of V), bytes of device factor tables. */
+fio_status bf_info(const fio_bf* bf, int64_t* out8);
+
+void bf_free(fio_bf* bf);
+
+/* ------------------------------------------------------------------------
+ * hss_build_from_samples -- randomized black-box HSS construction of the
+ *   Hermitian H given by `sampler` (Section 3.1-3.3), over an index set of
+ *   size N split into 2^Lh leaves of size `leaf` (N = leaf * 2^Lh, Lh >= 1,
+ *   leaf <= 256).  Per level l an independent Gaussian test matrix with
+ *   s_l = rhat_l + m_l + p columns (p = `oversample`) is drawn from
+ *   Philox4x32-10 with key `seed` and counter (row, col, l, attempt), Box-Muller
+ *   to complex N(0,1) + i N(0,1).  rhat_l starts at m_l/2 and is doubled (new
+ *   attempt) while the truncated rank exceeds it.  Per node: orthonormal null
+ *   basis Gamma of Omega_tau, column-pivoted QR of Y_tau Gamma truncated where
+ *   |R_kk| <= tol * max_j ||Y_tau(:,j)||, one rank per level (the level
+ *   maximum), residual block D-check (Section 3.1), root H^[0] = Y^[0] Omega^+;
+ *   top-down postprocessing for B and leaf D (Section 3.3).
+ *   Synchronizes `stream` (ranks are decided on the host).
+ *   Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK.
+ * ---------------------------------------------------------------------- */
+fio_status hss_build_from_samples(const fio_sampler* sampler, int64_t N, int leaf, int oversample,
+                                  double tol, uint64_t seed, void* stream, fio_hss** out);
+
+/* hss_from_generators -- build a handle from host generators (tests, restart).
+ *   ranks[0..Lh] (ranks[0] = 0); U: concatenation over l = 1..Lh, node-major,
+ *   of column-major m_l x r_l blocks (m_Lh = leaf, m_l = 2 r_{l+1});
+ *   B: concatenation over l = 0..Lh-1, node-major, of column-major
+ *   r_{l+1} x r_{l+1} blocks (B_{alpha2,alpha1}); D: 2^Lh column-major
+ *   leaf x leaf blocks.  Host pointers, complex64, copied.  Synchronizes. */
+fio_status hss_from_generators(int64_t N, int leaf, const int* ranks, const void* U, const void* B,
+                               const void* D, void* stream, fio_hss** out);
+
+/* hss_info -- out[0] = N, out[1] = leaf, out[2] = Lh, out[3 + l] = r_l for
+ *   l = 0..Lh (needs 3 + Lh + 1 entries; max_out bounds the writes), and the
+ *   number of sample columns drawn is returned in *samples if non-NULL. */
+fio_status hss_info(const fio_hss* hss, int64_t* out, int max_out, int64_t* samples);
+
+/* hss_matvec -- Y = G~ X through the telescoping factorization (Eq. 2.8).
+ *   X, Y: device, N x k complex64, ld >= N, no overlap. */
+fio_status hss_matvec(const fio_hss* hss, const void* X, void* Y, int64_t ld, int k, void* stream);
+
+/* hss_ulv_factor -- ULV factorization of G~ (Section 2.4, Eq. 2.9-2.12):
+ *   per node a unitary Q with Q^* U = [0; U^_2] (QR of U with the R block
+ *   moved to the bottom), Cholesky of D-check_11, D^_21, Schur complement,
+ *   merge into the parent, Cholesky of the root.  Stored per node as the
+ *   single matrix W = [[L11^{-1}, 0], [-D^_21 L11^{-1}, I]] Q^* (the up pass
+ *   applies W, the down pass W^*).  Synchronizes.
+ *   Errors: FIO_ENOTHPD (a pivot <= 0), FIO_ENOMEM, FIO_ECUDA. */
+fio_status hss_ulv_factor(fio_hss* hss, void* stream);
+
+/* hss_solve -- X = G~^{-1} B by the ULV bottom-up / root / top-down passes.
+ *   B, X: device, N x k complex64, ld >= N; B may equal X. */
+fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int k, void* stream);
+
+/* fio_solve -- online stage f = G~^{-1} K~^* u (Eq. 4.2), plus `refine_steps`
+ *   steps of iterative refinement f += G~^{-1}(K~^* u - K~^* K~ f).
+ *   U, F: device, N x k complex64, ld >= N, no overlap. */
+fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
+                     int refine_steps, void* stream);
+
+void hss_free(fio_hss* hss);
+
+/* fio_last_error -- message of the last failing call on this thread. */
+const char* fio_last_error(void);
+
+/* fio_profile_enable -- diagnostics, not part of the method: while enabled,
+ *   every kernel launched by bf_apply, hss_solve and fio_solve is bracketed
+ *   by a pair of CUDA events recorded on its stream (two event records per
+ *   launch).  Process-wide, not thread safe. */
+fio_status fio_profile_enable(int on);
+
+/* fio_profile_report -- waits for the recorded events and writes one line
+ *   "kernel_name launches total_ms" per kernel into buf (NUL terminated),
+ *   then clears the record.  FIO_EINVAL if len is too small. */
+fio_status fio_profile_report(char* buf, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIO_H */

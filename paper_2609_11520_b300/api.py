@@ -1,0 +1,163 @@
+"""Python binding of the FIO library: argument marshalling over the C ABI.
+
+Vectors are complex64 CUDA tensors of shape (N,) (one vector) or (k, N)
+(k vectors, each row contiguous -- the column-major N x k block of the C ABI
+with leading dimension N).  Every computation runs in libfio_b300.so on the
+current CUDA stream.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import FioError, check, lib
+
+__all__ = ["BF", "HSS", "fio_solve", "FioError"]
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _block(x, n, name):
+    """(ptr, ld, k) of a (N,) or (k, N) complex64 CUDA tensor with unit inner stride."""
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64 or not x.is_cuda:
+        raise TypeError(f"{name}: expected a complex64 CUDA tensor")
+    if x.dim() == 1:
+        if x.shape[0] != n or x.stride(0) != 1:
+            raise ValueError(f"{name}: expected a contiguous vector of length {n}")
+        return x.data_ptr(), n, 1
+    if x.dim() != 2 or x.shape[1] != n or x.stride(1) != 1 or (x.shape[0] > 1 and x.stride(0) < n):
+        raise ValueError(f"{name}: expected shape (k, {n}) with rows contiguous")
+    return x.data_ptr(), (x.stride(0) if x.shape[0] > 1 else n), x.shape[0]
+
+
+class BF:
+    """Butterfly factorization K~ of the 1D FIO (bf_build / bf_apply)."""
+
+    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None):
+        ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
+        h = ctypes.c_void_p()
+        check(lib.bf_build(ctypes.byref(ph), int(n), 1, int(r), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n, self.r, self.phase, self.s = int(n), int(r), phase, float(s)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        o = (ctypes.c_int64 * 8)()
+        check(lib.bf_info(self._h, o))
+        return dict(zip(["n", "d", "r", "L", "h", "sU", "sV", "table_bytes"], list(o)))
+
+    def apply(self, X, adjoint=False, out=None, stream=None):
+        px, ld, k = _block(X, self.n, "X")
+        if out is None:
+            out = torch.empty_like(X)
+        py, ldy, ky = _block(out, self.n, "out")
+        if ky != k or ldy != ld:
+            raise ValueError("out must match X in shape and row stride")
+        check(lib.bf_apply(self._h, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k, int(bool(adjoint)),
+                           _stream(stream)))
+        return out
+
+    def adjoint(self, X, out=None, stream=None):
+        return self.apply(X, adjoint=True, out=out, stream=stream)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.bf_free(h)
+            self._h = ctypes.c_void_p()
+
+
+class HSS:
+    """HSS approximation G~ with its ULV factorization (hss_* calls)."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = int(n)
+        self.factored = False
+        self._keep = None
+
+    @classmethod
+    def from_samples(cls, bf=None, dense=None, n=None, leaf=128, oversample=10, tol=1e-3, seed=0, stream=None):
+        sm = _lib.Sampler()
+        if bf is not None:
+            sm.kind, sm.bf, n = _lib.SAMPLER_NORMAL, bf.handle.value, bf.n
+        else:
+            if dense is None or dense.dtype != torch.complex64 or not dense.is_cuda:
+                raise TypeError("dense sampler: complex64 CUDA tensor (N, N) expected")
+            n = dense.shape[0]
+            # The C ABI takes H column-major; the row-major storage of H^T is exactly that.
+            dense = dense.transpose(0, 1).contiguous()
+            sm.kind, sm.dense, sm.ld = _lib.SAMPLER_DENSE, dense.data_ptr(), dense.stride(0)
+        h = ctypes.c_void_p()
+        check(lib.hss_build_from_samples(ctypes.byref(sm), int(n), int(leaf), int(oversample), float(tol),
+                                         ctypes.c_uint64(int(seed)), _stream(stream), ctypes.byref(h)))
+        obj = cls(h, n)
+        obj._keep = (bf, dense)
+        return obj
+
+    @classmethod
+    def from_generators(cls, n, leaf, ranks, U, B, D, stream=None):
+        """Host generators (numpy complex arrays in the C layout, see hss_from_generators)."""
+        import numpy as np
+        rk = (ctypes.c_int * len(ranks))(*[int(v) for v in ranks])
+        Ua = np.ascontiguousarray(U, dtype=np.complex64)
+        Ba = np.ascontiguousarray(B, dtype=np.complex64)
+        Da = np.ascontiguousarray(D, dtype=np.complex64)
+        h = ctypes.c_void_p()
+        check(lib.hss_from_generators(int(n), int(leaf), rk, Ua.ctypes.data_as(ctypes.c_void_p),
+                                      Ba.ctypes.data_as(ctypes.c_void_p), Da.ctypes.data_as(ctypes.c_void_p),
+                                      _stream(stream), ctypes.byref(h)))
+        return cls(h, n)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        o = (ctypes.c_int64 * 64)()
+        smp = ctypes.c_int64()
+        check(lib.hss_info(self._h, o, 64, ctypes.byref(smp)))
+        Lh = int(o[2])
+        return dict(N=int(o[0]), leaf=int(o[1]), Lh=Lh, ranks=[int(o[3 + l]) for l in range(Lh + 1)],
+                    samples=int(smp.value))
+
+    def matvec(self, X, out=None, stream=None):
+        px, ld, k = _block(X, self.n, "X")
+        out = torch.empty_like(X) if out is None else out
+        py, _, _ = _block(out, self.n, "out")
+        check(lib.hss_matvec(self._h, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k, _stream(stream)))
+        return out
+
+    def factor(self, stream=None):
+        check(lib.hss_ulv_factor(self._h, _stream(stream)))
+        self.factored = True
+        return self
+
+    def solve(self, Bm, out=None, stream=None):
+        px, ld, k = _block(Bm, self.n, "B")
+        out = torch.empty_like(Bm) if out is None else out
+        py, _, _ = _block(out, self.n, "out")
+        check(lib.hss_solve(self._h, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k, _stream(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.hss_free(h)
+            self._h = ctypes.c_void_p()
+
+
+def fio_solve(bf, hss, U, out=None, refine_steps=0, stream=None):
+    """f = G~^{-1} K~^* u (+ refinement steps)."""
+    px, ld, k = _block(U, bf.n, "U")
+    out = torch.empty_like(U) if out is None else out
+    py, _, _ = _block(out, bf.n, "F")
+    check(lib.fio_solve(bf.handle, hss.handle, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k,
+                        int(refine_steps), _stream(stream)))
+    return out

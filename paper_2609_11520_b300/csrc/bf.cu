@@ -1,0 +1,467 @@
+// Butterfly factorization: device evaluation of the factors (bf_build) and
+// the forward / adjoint products (bf_apply), Section 2.2, Eq. 2.1.
+#include <cmath>
+#include <cstring>
+
+#include "bf.cuh"
+
+namespace fio {
+namespace {
+
+constexpr int kMaxR = 16;   // rank bound of the warp-per-quad transfer kernels
+
+struct PhaseDev {
+    int kind;
+    double s;
+};
+struct Cheb {
+    double t[32];
+};
+
+// Phi(x, xi) of the 1D families (Eq. 1.1 with the phases of the workloads).
+__device__ __forceinline__ double phi(const PhaseDev& p, double x, double xi) {
+    double v = x * xi;
+    if (p.kind == FIO_PHASE_1D_CABS) v += (2.0 + p.s * sinpi(2.0 * x)) * 0.0625 * fabs(xi);
+    return v;
+}
+
+// e^{2 pi i ph} for an FP64 phase: reduce modulo 1 in FP64, then sin/cos of
+// the small remainder.
+__device__ __forceinline__ float2 expi2pi(double ph) {
+    double fr = ph - rint(ph);
+    float sn, cs;
+    sincospif(2.0f * float(fr), &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+__device__ __forceinline__ double space_center(int s, int64_t a) { return ldexp(double(a) + 0.5, -s); }
+__device__ __forceinline__ double space_node(const Cheb& c, int s, int64_t a, int k) {
+    return space_center(s, a) + ldexp(0.5, -s) * c.t[k];
+}
+__device__ __forceinline__ double freq_center(int n, int l, int64_t b) {
+    return -0.5 * n + (double(b) + 0.5) * ldexp(double(n), -l);
+}
+__device__ __forceinline__ double freq_node(const Cheb& c, int n, int l, int64_t b, int k) {
+    return freq_center(n, l, b) + ldexp(double(n), -l - 1) * c.t[k];
+}
+
+// ---------------------------------------------------------------- tables
+__global__ void k_tab_VP(float2* VP, PhaseDev ph, int n, int sV) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t total = (int64_t(1) << sV) * n;
+    if (e >= total) return;
+    int64_t a = e / n, j = e % n;
+    VP[e] = expi2pi(phi(ph, space_center(sV, a), double(j) - 0.5 * n));
+}
+
+__global__ void k_tab_UP(float2* UP, PhaseDev ph, int n, int L, int sU) {
+    int nb = 1 << (L - sU);
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(n) * nb) return;
+    int64_t i = e / nb, b = e % nb;
+    UP[e] = expi2pi(phi(ph, double(i) / n, freq_center(n, L - sU, b)));
+}
+
+// F_s[q][c][beta][t], quad q = (tau at space level s, b' at frequency level L-s-1).
+__global__ void k_tab_F(float2* F, PhaseDev ph, Cheb ch, int n, int L, int s, int r) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t nquad = int64_t(n) / 2;
+    if (e >= nquad * 4 * r) return;
+    int t = int(e % r);
+    int64_t rest = e / r;
+    int be = int(rest & 1), c = int((rest >> 1) & 1);
+    int64_t q = rest >> 2;
+    int64_t nbq = int64_t(1) << (L - s - 1);
+    int64_t tau = q / nbq, bq = q % nbq;
+    double g = freq_node(ch, n, L - s, 2 * bq + be, t);
+    double yc = space_center(s + 1, 2 * tau + c), yp = space_center(s, tau);
+    F[e] = expi2pi(phi(ph, yc, g) - phi(ph, yp, g));
+}
+
+// E_s[q][c][beta][i], quad q = (alpha at space level s, b' at frequency level L-s-1).
+__global__ void k_tab_E(float2* E, PhaseDev ph, Cheb ch, int n, int L, int s, int r) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t nquad = int64_t(n) / 2;
+    if (e >= nquad * 4 * r) return;
+    int i = int(e % r);
+    int64_t rest = e / r;
+    int be = int(rest & 1), c = int((rest >> 1) & 1);
+    int64_t q = rest >> 2;
+    int64_t nbq = int64_t(1) << (L - s - 1);
+    int64_t al = q / nbq, bq = q % nbq;
+    double z = space_node(ch, s + 1, 2 * al + c, i);
+    E[e] = expi2pi(phi(ph, z, freq_center(n, L - s, 2 * bq + be)) - phi(ph, z, freq_center(n, L - s - 1, bq)));
+}
+
+// M[p][i][j], pair p = tau * 2^(L-h) + sigma at the middle level h.
+__global__ void k_tab_M(float2* M, PhaseDev ph, Cheb ch, int n, int L, int h, int r) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(n) * r * r) return;
+    int j = int(e % r), i = int((e / r) % r);
+    int64_t p = e / (int64_t(r) * r);
+    int64_t nb = int64_t(1) << (L - h);
+    int64_t tau = p / nb, sg = p % nb;
+    double z = space_node(ch, h, tau, i), y = space_center(h, tau);
+    double g = freq_node(ch, n, L - h, sg, j), eta = freq_center(n, L - h, sg);
+    M[e] = expi2pi(phi(ph, z, g) - phi(ph, z, eta) - phi(ph, y, g));
+}
+
+// ---------------------------------------------------------------- apply
+// V: c(a,b,j) = sum_q PV[q][j] VP[a][b ls + q] x(b ls + q)
+__global__ void k_V_fwd(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S, const float2* __restrict__ VP,
+                        const float* __restrict__ PV, int n, int L, int sV, int r) {
+    extern __shared__ float sP[];
+    int ls = 1 << sV, nb = 1 << (L - sV);
+    for (int e = threadIdx.x; e < ls * r; e += blockDim.x) sP[e] = PV[e];
+    __syncthreads();
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (e >= int64_t(n) * r) return;
+    int j = int(e % r);
+    int64_t p = e / r, a = p / nb, b = p % nb;
+    const float2* x = X + col * ld + b * ls;
+    const float2* vp = VP + a * n + b * ls;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < ls; ++q) {
+        float2 v = cmul(vp[q], x[q]);
+        acc.x = fmaf(sP[q * r + j], v.x, acc.x);
+        acc.y = fmaf(sP[q * r + j], v.y, acc.y);
+    }
+    S[int64_t(col) * n * r + e] = acc;
+}
+
+// V^*: f(j) = sum_a conj(VP[a][j]) sum_t PV[q][t] c(a,b,t),  j = b ls + q
+__global__ void k_V_adj(const float2* __restrict__ S, float2* __restrict__ Y, int64_t ld, const float2* __restrict__ VP,
+                        const float* __restrict__ PV, int n, int L, int sV, int r) {
+    extern __shared__ float sP[];
+    int ls = 1 << sV, nb = 1 << (L - sV), na = 1 << sV;
+    for (int e = threadIdx.x; e < ls * r; e += blockDim.x) sP[e] = PV[e];
+    __syncthreads();
+    int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (j >= n) return;
+    int64_t b = j / ls;
+    int q = int(j % ls);
+    const float2* st = S + int64_t(col) * n * r;
+    float2 out = make_float2(0.f, 0.f);
+    for (int a = 0; a < na; ++a) {
+        const float2* c = st + (int64_t(a) * nb + b) * r;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int t = 0; t < r; ++t) {
+            acc.x = fmaf(sP[q * r + t], c[t].x, acc.x);
+            acc.y = fmaf(sP[q * r + t], c[t].y, acc.y);
+        }
+        cfmac(out, VP[int64_t(a) * n + j], acc);
+    }
+    Y[col * ld + j] = out;
+}
+
+// U: y(x) = sum_b UP[x][b] sum_i PU[q][i] d(a,b,i),  x = a ls + q
+__global__ void k_U_fwd(const float2* __restrict__ S, float2* __restrict__ Y, int64_t ld, const float2* __restrict__ UP,
+                        const float* __restrict__ PU, int n, int L, int sU, int r) {
+    extern __shared__ float sP[];
+    int ls = 1 << (L - sU), nb = ls;
+    for (int e = threadIdx.x; e < ls * r; e += blockDim.x) sP[e] = PU[e];
+    __syncthreads();
+    int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (x >= n) return;
+    int64_t a = x / ls;
+    int q = int(x % ls);
+    const float2* st = S + int64_t(col) * n * r;
+    float2 out = make_float2(0.f, 0.f);
+    for (int b = 0; b < nb; ++b) {
+        const float2* d = st + (a * nb + b) * r;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i < r; ++i) {
+            acc.x = fmaf(sP[q * r + i], d[i].x, acc.x);
+            acc.y = fmaf(sP[q * r + i], d[i].y, acc.y);
+        }
+        cfma(out, UP[x * nb + b], acc);
+    }
+    Y[col * ld + x] = out;
+}
+
+// U^*: d(a,b,i) = sum_q PU[q][i] conj(UP[a ls + q][b]) g(a ls + q)
+__global__ void k_U_adj(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S, const float2* __restrict__ UP,
+                        const float* __restrict__ PU, int n, int L, int sU, int r) {
+    extern __shared__ float sP[];
+    int ls = 1 << (L - sU), nb = ls;
+    for (int e = threadIdx.x; e < ls * r; e += blockDim.x) sP[e] = PU[e];
+    __syncthreads();
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (e >= int64_t(n) * r) return;
+    int i = int(e % r);
+    int64_t p = e / r, a = p / nb, b = p % nb;
+    const float2* g = X + col * ld + a * ls;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < ls; ++q) {
+        float2 v = cmulc(UP[(a * ls + q) * nb + b], g[q]);
+        acc.x = fmaf(sP[q * r + i], v.x, acc.x);
+        acc.y = fmaf(sP[q * r + i], v.y, acc.y);
+    }
+    S[int64_t(col) * n * r + e] = acc;
+}
+
+// M (forward): d(p,i) = sum_j M[p][i][j] c(p,j);  M^*: c(p,j) = sum_i conj(M[p][i][j]) d(p,i)
+template <bool ADJ>
+__global__ void k_M(const float2* __restrict__ Sin, float2* __restrict__ Sout, const float2* __restrict__ M, int n, int r) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (e >= int64_t(n) * r) return;
+    int o = int(e % r);
+    int64_t p = e / r;
+    const float2* x = Sin + int64_t(col) * n * r + p * r;
+    const float2* m = M + p * r * r;
+    float2 acc = make_float2(0.f, 0.f);
+    if (!ADJ) {
+        for (int j = 0; j < r; ++j) cfma(acc, m[o * r + j], x[j]);
+    } else {
+        for (int i = 0; i < r; ++i) cfmac(acc, m[i * r + o], x[i]);
+    }
+    Sout[int64_t(col) * n * r + e] = acc;
+}
+
+// Transfer factor on quads (warp per quad, r <= 16; lane = (half, index)).
+//  MS ("mix, then scale"):  y[o][i] = sum_e Phi(o,e,i) sum_t Pc[o][i][t] x[e][t]
+//        forward B (table E[q][o][e]) / adjoint C (conj F[q][e][o])
+//  SM ("scale, then mix"):  y[o][j] = sum_e sum_t Pc[e][t][j] Phi(o,e,t) x[e][t]
+//        forward C (table F[q][o][e]) / adjoint B (conj E[q][e][o])
+//  Forward: inputs are the pairs (tau, 2b'+e) (adjacent), outputs (2tau+o, b').
+//  Adjoint: the reverse.
+template <bool MS, bool ADJ>
+__global__ void k_quad(const float2* __restrict__ Sin, float2* __restrict__ Sout, const float2* __restrict__ T,
+                       const float* __restrict__ Pc, int n, int L, int s, int r) {
+    __shared__ float sPc[2 * kMaxR * kMaxR];
+    __shared__ float2 sx[8][2 * kMaxR];
+    __shared__ float2 sg[8][4 * kMaxR];
+    for (int e = threadIdx.x; e < 2 * r * r; e += blockDim.x) sPc[e] = Pc[e];
+    __syncthreads();
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t q = int64_t(blockIdx.x) * 8 + w;
+    int col = blockIdx.y;
+    int64_t nquad = int64_t(n) / 2;
+    if (q >= nquad) return;
+    int64_t nbq = int64_t(1) << (L - s - 1);
+    int64_t tau = q / nbq, bq = q % nbq;
+    const float2* in = Sin + int64_t(col) * n * r;
+    float2* out = Sout + int64_t(col) * n * r;
+    int hl = lane >> 4, idx = lane & 15;
+    bool act = idx < r;
+    // pair indices
+    int64_t pin, pout;
+    if (!ADJ) {
+        pin = tau * 2 * nbq + 2 * bq + hl;
+        pout = (2 * tau + hl) * nbq + bq;
+    } else {
+        pin = (2 * tau + hl) * nbq + bq;
+        pout = tau * 2 * nbq + 2 * bq + hl;
+    }
+    if (act) sx[w][hl * r + idx] = in[pin * r + idx];
+    __syncwarp();
+    const float2* tq = T + q * 4 * r;
+    float2 y = make_float2(0.f, 0.f);
+    if (MS) {
+        // lane = (o = hl, i = idx)
+        if (act) {
+            const float* P = sPc + hl * r * r + idx * r;
+            float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
+            for (int t = 0; t < r; ++t) {
+                float pv = P[t];
+                float2 x0 = sx[w][t], x1 = sx[w][r + t];
+                h0.x = fmaf(pv, x0.x, h0.x); h0.y = fmaf(pv, x0.y, h0.y);
+                h1.x = fmaf(pv, x1.x, h1.x); h1.y = fmaf(pv, x1.y, h1.y);
+            }
+            if (!ADJ) {
+                cfma(y, tq[(hl * 2 + 0) * r + idx], h0);
+                cfma(y, tq[(hl * 2 + 1) * r + idx], h1);
+            } else {
+                cfmac(y, tq[(0 * 2 + hl) * r + idx], h0);
+                cfmac(y, tq[(1 * 2 + hl) * r + idx], h1);
+            }
+            out[pout * r + idx] = y;
+        }
+    } else {
+        // g[o][e][t] = Phi(o,e,t) x[e][t]; lane (e = hl, t = idx) computes both o
+        if (act) {
+            float2 xv = sx[w][hl * r + idx];
+            for (int o = 0; o < 2; ++o) {
+                float2 g;
+                if (!ADJ) g = cmul(tq[(o * 2 + hl) * r + idx], xv);
+                else g = cmulc(tq[(hl * 2 + o) * r + idx], xv);
+                sg[w][(o * 2 + hl) * r + idx] = g;
+            }
+        }
+        __syncwarp();
+        // lane = (o = hl, j = idx)
+        if (act) {
+            for (int e2 = 0; e2 < 2; ++e2) {
+                const float* P = sPc + e2 * r * r;
+                for (int t = 0; t < r; ++t) {
+                    float pv = P[t * r + idx];
+                    float2 g = sg[w][(hl * 2 + e2) * r + t];
+                    y.x = fmaf(pv, g.x, y.x);
+                    y.y = fmaf(pv, g.y, y.y);
+                }
+            }
+            out[pout * r + idx] = y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host helpers
+double lagrange_host(const double* t, int r, int k, double u) {
+    double v = 1.0;
+    for (int kk = 0; kk < r; ++kk)
+        if (kk != k) v *= (u - t[kk]) / (t[k] - t[kk]);
+    return v;
+}
+
+}  // namespace
+
+fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
+                         float2* s0, float2* s1, cudaStream_t st) {
+    const int n = bf->n, r = bf->r, L = bf->L;
+    const float* P = bf->P.as<float>();
+    const float* PV = P + bf->pv_off();
+    const float* PU = P + bf->pu_off();
+    const float* Pc = P + bf->pc_off();
+    const int TB = 256;
+    dim3 gNr(cdiv(int64_t(n) * r, TB), kc), gN(cdiv(n, TB), kc), gQ(cdiv(int64_t(n) / 2, 8), kc);
+    size_t shV = size_t(bf->lsV) * r * sizeof(float), shU = size_t(bf->lsU) * r * sizeof(float);
+    float2* a = s0;
+    float2* b = s1;
+    if (!adjoint) {
+        FIO_LAUNCH("k_V_fwd", st, k_V_fwd<<<gNr, TB, shV, st>>>(X, ld, a, bf->VP.as<float2>(), PV, n, L, bf->sV, r));
+        for (int s = bf->sV; s < bf->h; ++s) {
+            FIO_LAUNCH("k_quad_C_fwd", st, k_quad<false, false><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, s, r));
+            std::swap(a, b);
+        }
+        FIO_LAUNCH("k_M_fwd", st, k_M<false><<<gNr, TB, 0, st>>>(a, b, bf->M.as<float2>(), n, r));
+        std::swap(a, b);
+        for (int s = bf->h; s < bf->sU; ++s) {
+            FIO_LAUNCH("k_quad_B_fwd", st, k_quad<true, false><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, s, r));
+            std::swap(a, b);
+        }
+        FIO_LAUNCH("k_U_fwd", st, k_U_fwd<<<gN, TB, shU, st>>>(a, Y, ld, bf->UP.as<float2>(), PU, n, L, bf->sU, r));
+    } else {
+        FIO_LAUNCH("k_U_adj", st, k_U_adj<<<gNr, TB, shU, st>>>(X, ld, a, bf->UP.as<float2>(), PU, n, L, bf->sU, r));
+        for (int s = bf->sU - 1; s >= bf->h; --s) {
+            FIO_LAUNCH("k_quad_B_adj", st, k_quad<false, true><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, s, r));
+            std::swap(a, b);
+        }
+        FIO_LAUNCH("k_M_adj", st, k_M<true><<<gNr, TB, 0, st>>>(a, b, bf->M.as<float2>(), n, r));
+        std::swap(a, b);
+        for (int s = bf->h - 1; s >= bf->sV; --s) {
+            FIO_LAUNCH("k_quad_C_adj", st, k_quad<true, true><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, s, r));
+            std::swap(a, b);
+        }
+        FIO_LAUNCH("k_V_adj", st, k_V_adj<<<gN, TB, shV, st>>>(a, Y, ld, bf->VP.as<float2>(), PV, n, L, bf->sV, r));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+}  // namespace fio
+
+using namespace fio;
+
+extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, fio_bf** out) {
+    if (!out || !phase) return fail(FIO_EINVAL, "bf_build: null pointer");
+    *out = nullptr;
+    if (d != 1) return fail(FIO_EINVAL, "bf_build: only d = 1 is supported");
+    int L = ilog2_exact(n);
+    if (L < 4 || L > 24) return fail(FIO_EINVAL, "bf_build: n must be a power of two in [16, 2^24]");
+    if (r < 1 || r > kMaxR) return fail(FIO_EINVAL, "bf_build: r must be in [1, 16]");
+    if (phase->kind != FIO_PHASE_DFT && phase->kind != FIO_PHASE_1D_CABS)
+        return fail(FIO_EINVAL, "bf_build: unknown phase kind");
+    cudaStream_t st = as_stream(stream);
+    fio_bf* bf = new fio_bf();
+    bf->phase = *phase;
+    bf->n = n; bf->d = d; bf->r = r; bf->L = L;
+    bf->h = L / 2;
+    bf->sU = std::max(L - 3, bf->h);
+    bf->sV = std::min(3, bf->h);
+    bf->lsV = 1 << bf->sV;
+    bf->lsU = 1 << (L - bf->sU);
+    for (int k = 0; k < 32; ++k) bf->tcheb[k] = k < r ? std::cos((2.0 * k + 1.0) * M_PI / (2.0 * r)) : 0.0;
+    PhaseDev ph{phase->kind, phase->s};
+    Cheb ch;
+    std::memcpy(ch.t, bf->tcheb, sizeof(ch.t));
+    auto cleanup = [&](fio_status s) { bf_free(bf); return s; };
+    // real Lagrange tables
+    std::vector<float> P(size_t(bf->lsV) * r + size_t(bf->lsU) * r + 2 * size_t(r) * r);
+    for (int q = 0; q < bf->lsV; ++q)
+        for (int j = 0; j < r; ++j) P[bf->pv_off() + q * r + j] = float(lagrange_host(bf->tcheb, r, j, 2.0 * q / bf->lsV - 1.0));
+    for (int q = 0; q < bf->lsU; ++q)
+        for (int i = 0; i < r; ++i) P[bf->pu_off() + q * r + i] = float(lagrange_host(bf->tcheb, r, i, 2.0 * q / bf->lsU - 1.0));
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < r; ++i)
+            for (int t = 0; t < r; ++t)
+                P[bf->pc_off() + (c * r + i) * r + t] = float(lagrange_host(bf->tcheb, r, t, (c - 0.5) + 0.5 * bf->tcheb[i]));
+    fio_status s;
+    if ((s = bf->P.ensure(P.size() * sizeof(float))) != FIO_OK) return cleanup(s);
+    if (cudaMemcpyAsync(bf->P.p, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return cleanup(cuda_status(cudaGetLastError(), "bf_build: copy of Lagrange tables"));
+    const int TB = 256;
+    int64_t nVP = (int64_t(1) << bf->sV) * n, nUP = int64_t(n) * bf->lsU;
+    int64_t nM = int64_t(n) * r * r, nT = int64_t(n) / 2 * 4 * r;
+    if ((s = bf->VP.ensure(nVP * 8)) != FIO_OK) return cleanup(s);
+    if ((s = bf->UP.ensure(nUP * 8)) != FIO_OK) return cleanup(s);
+    if ((s = bf->M.ensure(nM * 8)) != FIO_OK) return cleanup(s);
+    k_tab_VP<<<cdiv(nVP, TB), TB, 0, st>>>(bf->VP.as<float2>(), ph, n, bf->sV);
+    k_tab_UP<<<cdiv(nUP, TB), TB, 0, st>>>(bf->UP.as<float2>(), ph, n, L, bf->sU);
+    k_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), ph, ch, n, L, bf->h, r);
+    bf->C.resize(bf->h - bf->sV);
+    for (int lv = bf->sV; lv < bf->h; ++lv) {
+        if ((s = bf->C[lv - bf->sV].ensure(nT * 8)) != FIO_OK) return cleanup(s);
+        k_tab_F<<<cdiv(nT, TB), TB, 0, st>>>(bf->C[lv - bf->sV].as<float2>(), ph, ch, n, L, lv, r);
+    }
+    bf->B.resize(bf->sU - bf->h);
+    for (int lv = bf->h; lv < bf->sU; ++lv) {
+        if ((s = bf->B[lv - bf->h].ensure(nT * 8)) != FIO_OK) return cleanup(s);
+        k_tab_E<<<cdiv(nT, TB), TB, 0, st>>>(bf->B[lv - bf->h].as<float2>(), ph, ch, n, L, lv, r);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_status(e, "bf_build: table kernels"));
+    bf->table_bytes = (nVP + nUP + nM + nT * int64_t(bf->C.size() + bf->B.size())) * 8 + int64_t(P.size()) * 4;
+    *out = bf;
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream) {
+    if (!bf) return fail(FIO_EINVAL, "bf_apply: null handle");
+    if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
+    if (k == 0) return FIO_OK;
+    if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
+    const int64_t stateN = int64_t(bf->n) * bf->r;
+    // column chunk: at most 64 columns or 1 GiB of state, whichever is smaller
+    int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(1) << 30) / (2 * stateN * 8)))));
+    FIO_TRY(bf->ws.ensure(size_t(2) * stateN * kc * 8));
+    float2* s0 = bf->ws.as<float2>();
+    float2* s1 = s0 + stateN * kc;
+    cudaStream_t st = as_stream(stream);
+    for (int c0 = 0; c0 < k; c0 += kc) {
+        int cc = std::min(kc, k - c0);
+        FIO_TRY(bf_apply_cols(bf, reinterpret_cast<const float2*>(X) + c0 * ld, reinterpret_cast<float2*>(Y) + c0 * ld,
+                              ld, cc, adjoint, s0, s1, st));
+    }
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_info(const fio_bf* bf, int64_t* o) {
+    if (!bf || !o) return fail(FIO_EINVAL, "bf_info: null pointer");
+    o[0] = bf->n; o[1] = bf->d; o[2] = bf->r; o[3] = bf->L; o[4] = bf->h; o[5] = bf->sU; o[6] = bf->sV;
+    o[7] = bf->table_bytes;
+    return FIO_OK;
+}
+
+extern "C" void bf_free(fio_bf* bf) {
+    if (!bf) return;
+    bf->VP.release(); bf->UP.release(); bf->M.release(); bf->P.release(); bf->ws.release();
+    for (auto& b : bf->C) b.release();
+    for (auto& b : bf->B) b.release();
+    delete bf;
+}

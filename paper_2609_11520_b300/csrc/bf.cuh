@@ -1,0 +1,46 @@
+// Butterfly factorization handle (Section 2.2, Eq. 2.1), device-resident.
+//
+// The factors are stored in a phase-folded factored form that is
+// mathematically identical to Eq. 2.1.  Every transfer block of Eq. 2.4-2.6
+// is  diag(phase) * P * diag(phase)  with P a real Lagrange matrix shared by
+// all boxes of a level (dyadic boxes are scaled copies of each other).  The
+// two diagonal phases of consecutive factors are merged into one table per
+// level, so that the coefficient state between stages is expressed in
+// "demodulated" bases:
+//   c^(s)(tau,sigma,j)  stored as  e^{+2 pi i Phi(y_tau, gamma_sigma_j)} c   (right side)
+//   d^(s)(tau,sigma,i)  stored as  e^{-2 pi i Phi(z_tau_i, eta_sigma)} d     (left side)
+// Tables (complex64):
+//   VP[a][j]        e^{2 pi i Phi(y_a, xi_j)}            a: space box of level sV
+//   F_s[q][c][b][t] e^{2 pi i (Phi(y_tau', gamma_bt) - Phi(y_tau, gamma_bt))}   C level s
+//   M[p][i][j]      e^{2 pi i (Phi(z_i, gamma_j) - Phi(z_i, eta) - Phi(y, gamma_j))}
+//   E_s[q][c][b][i] e^{2 pi i (Phi(z_tau_i, eta_beta) - Phi(z_tau_i, eta_sigma))} B level s
+//   UP[x][b]        e^{2 pi i Phi(x, eta_b)}              b: frequency box of level L-sU
+// and real tables PV[q][j], PU[q][i] (Lagrange basis at the leaf points) and
+// Pc[c][i][t] = l_t((c - 1/2) + t_i / 2) (parent basis at the child nodes).
+// A "quad" q = (space box at level s, frequency box b' at level L-s-1)
+// couples the two input pairs (tau, 2b'+e) with the two output pairs
+// (2 tau + o, b').
+#pragma once
+#include "common.cuh"
+
+struct fio_bf {
+    fio_phase phase;
+    int n = 0, d = 1, r = 0, L = 0, h = 0, sU = 0, sV = 0;
+    int lsV = 0, lsU = 0;          // points per V frequency leaf / per U space leaf
+    double tcheb[32];              // Chebyshev points on [-1, 1]
+    fio::DevBuf VP, UP, M, P;      // P: PV | PU | Pc (float)
+    std::vector<fio::DevBuf> C;    // index s - sV
+    std::vector<fio::DevBuf> B;    // index s - h
+    fio::DevBuf ws;                // two coefficient states
+    int64_t table_bytes = 0;
+    int64_t N() const { return int64_t(n); }
+    size_t pv_off() const { return 0; }
+    size_t pu_off() const { return size_t(lsV) * r; }
+    size_t pc_off() const { return size_t(lsV) * r + size_t(lsU) * r; }
+};
+
+namespace fio {
+// Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
+fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
+                         float2* s0, float2* s1, cudaStream_t st);
+}

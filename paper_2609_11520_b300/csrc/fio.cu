@@ -1,0 +1,55 @@
+// Online stage of Algorithm 1: f = G~^{-1} K~^* u (Eq. 4.2), with optional
+// iterative refinement on the approximate normal equation (Eq. 4.3):
+//   f <- f + G~^{-1} (K~^* u - K~^* K~ f).
+#include "bf.cuh"
+#include "hss.cuh"
+
+namespace fio {
+namespace {
+// r = a - b ; f += d  (column blocks, ld)
+__global__ void k_sub(const float2* __restrict__ a, const float2* __restrict__ b, float2* __restrict__ r, int64_t n,
+                      int64_t lda, int64_t ldb, int64_t ldr) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (i < n) r[col * ldr + i] = csub(a[col * lda + i], b[col * ldb + i]);
+}
+__global__ void k_add(float2* __restrict__ f, const float2* __restrict__ d, int64_t n, int64_t ldf, int64_t ldd) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (i < n) f[col * ldf + i] = cadd(f[col * ldf + i], d[col * ldd + i]);
+}
+}  // namespace
+}  // namespace fio
+
+using namespace fio;
+
+extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, void* F, int64_t ld, int k, int refine_steps,
+                                void* stream) {
+    if (!bf || !hc) return fail(FIO_EINVAL, "fio_solve: null handle");
+    if (bf->N() != hc->N) return fail(FIO_EINVAL, "fio_solve: BF and HSS sizes differ");
+    if (k < 0 || ld < hc->N || refine_steps < 0) return fail(FIO_EINVAL, "fio_solve: bad k, ld or refine_steps");
+    if (k == 0) return FIO_OK;
+    if (!U || !F) return fail(FIO_EINVAL, "fio_solve: null vector");
+    fio_hss* h = const_cast<fio_hss*>(hc);
+    cudaStream_t st = as_stream(stream);
+    const int64_t N = h->N;
+    const int nbuf = refine_steps > 0 ? 3 : 1;
+    FIO_TRY(h->fio_ws.ensure(size_t(nbuf) * ld * k * 8));
+    float2* T = h->fio_ws.as<float2>();
+    FIO_TRY(bf_apply(bf, U, T, ld, k, 1, st));                 // T = K~^* u (ld of the caller's block)
+    FIO_TRY(hss_solve(h, T, F, ld, k, st));                    // f = G~^{-1} T
+    if (refine_steps > 0) {
+        float2* R1 = T + ld * k;
+        float2* R2 = R1 + ld * k;
+        dim3 g(cdiv(N, 256), k);
+        for (int it = 0; it < refine_steps; ++it) {
+            FIO_TRY(bf_apply(bf, F, R1, ld, k, 0, st));        // K~ f
+            FIO_TRY(bf_apply(bf, R1, R2, ld, k, 1, st));       // K~^* K~ f
+            FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T, R2, R1, N, ld, ld, ld));   // residual of Eq. 4.3
+            FIO_TRY(hss_solve(h, R1, R2, ld, k, st));
+            FIO_LAUNCH("k_add", st, k_add<<<g, 256, 0, st>>>(static_cast<float2*>(F), R2, N, ld, ld));
+        }
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}

@@ -1,0 +1,35 @@
+// HSS handle (Def. 2.1-2.2) with one rank per level, and its ULV factors
+// (Section 2.4).  All generator blocks are complex64, column-major,
+// node-major within a level.
+#pragma once
+#include "common.cuh"
+
+struct fio_hss {
+    int64_t N = 0;
+    int leaf = 0, Lh = 0;
+    std::vector<int> ranks;          // r_l, l = 0..Lh (r_0 = 0)
+    std::vector<fio::DevBuf> U;      // U[l], l = 1..Lh: 2^l blocks m_l x r_l
+    std::vector<fio::DevBuf> B;      // B[l], l = 0..Lh-1: 2^l blocks r_{l+1} x r_{l+1}
+    fio::DevBuf D;                   // 2^Lh blocks leaf x leaf
+    // ULV factors: W[l] (2^l blocks m_l x m_l, complex64), root inverse
+    bool factored = false;
+    std::vector<fio::DevBuf> W;
+    fio::DevBuf Rinv;                // m_0 x m_0 (complex64)
+    fio::DevBuf solve_ws;            // per-level vectors of the solve
+    fio::DevBuf mv_ws;               // per-level vectors of the matvec
+    fio::DevBuf fio_ws;              // K~^* u and refinement vectors of fio_solve
+    int64_t samples = 0;
+    int m(int l) const { return l == Lh ? leaf : 2 * ranks[l + 1]; }
+    int64_t rows(int l) const { return (int64_t(1) << l) * m(l); }   // sum of m over level l
+    int64_t rrows(int l) const { return (int64_t(1) << l) * ranks[l]; }
+};
+
+namespace fio {
+// Block products over the nodes of level l (column-major vectors, ld = rows):
+//   expand:   out[t*m + i] (+)= sum_c U_t[i][c] in[t*r + c]
+//   compress: out[t*r + c]  = sum_i conj(U_t[i][c]) in[t*m + i]
+void launch_expand(const float2* U, int nodes, int m, int r, const float2* in, int64_t ldin, float2* out,
+                   int64_t ldout, int k, bool accumulate, cudaStream_t st);
+void launch_compress(const float2* U, int nodes, int m, int r, const float2* in, int64_t ldin, float2* out,
+                     int64_t ldout, int k, cudaStream_t st);
+}

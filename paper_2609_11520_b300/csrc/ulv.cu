@@ -1,0 +1,524 @@
+// ULV factorization of the HSS matrix G~ (Section 2.4, Eq. 2.9-2.12) and the
+// bottom-up / root / top-down solve.
+//
+// Per node (D: m x m Hermitian, U: m x r with orthonormal columns):
+//   QR of U by r Householder reflectors, U = Q_r [R; 0].  Q = Q_r P with P
+//   moving the first r rows to the bottom gives Q^* U = [0; R]: U^_2 = R
+//   (basis elimination, Eq. 2.9).
+//   D-check = Q^* D Q; Cholesky D-check_11 = L11 L11^*; D^_21 = D-check_21 L11^{-*};
+//   D^_22 = D-check_22 - D^_21 D^_21^* (partial factorization, Eq. 2.10-2.11).
+//   The node keeps the single matrix
+//       W = [[L11^{-1} Q1^*], [Q2^* - D^_21 L11^{-1} Q1^*]]   (Q = [Q1 Q2])
+//   so that the up pass is [b^_1; y^_2] = W y and the down pass is
+//   c = Q [c^_1; c^_2] = W^* [b^_1; c^_2] with c^_1 = L11^{-*}(b^_1 - D^_21^* c^_2).
+//   Merge (Eq. 2.12): D+ = [[D^22_1, U^2_1 B^* U^2_2^*], [U^2_2 B U^2_1^*, D^22_2]],
+//   U+ = diag(U^2_1, U^2_2) U_parent.  Root: D+ = L L^*, stored as (L L^*)^{-1}.
+#include <algorithm>
+#include <cmath>
+
+#include "cplx.cuh"
+#include "hss.cuh"
+
+namespace fio {
+namespace {
+
+constexpr int TB = 256;
+constexpr int kFp64Nodes = 16;   // FP64 on levels with at most this many nodes
+
+template <class C>
+__device__ void zlarfg(C alpha, typename RealOf<C>::T xn, typename RealOf<C>::T& beta, C& tau, C& scal) {
+    using R = typename RealOf<C>::T;
+    if (xn == R(0) && alpha.y == R(0)) {
+        beta = alpha.x;
+        tau = czero<C>();
+        scal = czero<C>();
+    } else {
+        R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn);
+        beta = alpha.x >= 0 ? -nrm : nrm;
+        tau = mkc<C>((beta - alpha.x) / beta, -alpha.y / beta);
+        scal = gdiv(mkc<C>(1, 0), mkc<C>(alpha.x - beta, alpha.y));
+    }
+}
+
+// Node factorization.  Inputs: D (float2 Df or C Dc, column-major m x m),
+// U (float2 Uf or C Uc, column-major m x r).  Outputs: W (float2, column-major
+// m x m), D^22 and U^2 (C, column-major r x r).  Scratch per node (C):
+// Dw m*m | Qr m*m | A1 m*m | Ur m*r | Dh21 r*m | tau r.
+template <class C>
+__global__ void k_ulv_node(const float2* __restrict__ Df, const C* __restrict__ Dc, const float2* __restrict__ Uf,
+                           const C* __restrict__ Uc, int m, int r, float2* __restrict__ Wout, C* __restrict__ Dh22,
+                           C* __restrict__ Uh2, C* __restrict__ scr, int* status) {
+    using R = typename RealOf<C>::T;
+    __shared__ R red[32];
+    const int t = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+    const int n1 = m - r;
+    const int64_t mm = int64_t(m) * m;
+    C* Dw = scr + int64_t(t) * (3 * mm + 2 * int64_t(m) * r + r);
+    C* Qr = Dw + mm;
+    C* A1 = Qr + mm;
+    C* Ur = A1 + mm;
+    C* Dh21 = Ur + int64_t(m) * r;
+    C* taus = Dh21 + int64_t(m) * r;
+    for (int64_t e = tid; e < mm; e += bd) Dw[e] = Df ? cvt<C>(Df[t * mm + e]) : Dc[t * mm + e];
+    for (int64_t e = tid; e < int64_t(m) * r; e += bd)
+        Ur[e] = Uf ? cvt<C>(Uf[t * int64_t(m) * r + e]) : Uc[t * int64_t(m) * r + e];
+    __syncthreads();
+    // QR of U
+    for (int k = 0; k < r; ++k) {
+        C* col = Ur + int64_t(k) * m;
+        R xn = 0;
+        for (int i = k + 1 + tid; i < m; i += bd) xn += gabs2(col[i]);
+        xn = block_sum(xn, red);
+        R beta;
+        C tau, scal;
+        zlarfg(col[k], xn, beta, tau, scal);
+        __syncthreads();
+        for (int i = k + 1 + tid; i < m; i += bd) col[i] = gmul(col[i], scal);
+        if (tid == 0) {
+            col[k] = mkc<C>(beta, 0);
+            taus[k] = tau;
+        }
+        __syncthreads();
+        for (int j = k + 1 + warp; j < r; j += nw) {
+            C* cj = Ur + int64_t(j) * m;
+            C w = lane == 0 ? cj[k] : czero<C>();
+            for (int i = k + 1 + lane; i < m; i += 32) gfmac(w, col[i], cj[i]);
+            w.x = warp_sum(w.x);
+            w.y = warp_sum(w.y);
+            C tw = gmulc(tau, w);
+            if (lane == 0) cj[k] = gsub(cj[k], tw);
+            for (int i = k + 1 + lane; i < m; i += 32) cj[i] = gsub(cj[i], gmul(col[i], tw));
+        }
+        __syncthreads();
+    }
+    // U^_2 = R
+    for (int e = tid; e < r * r; e += bd) {
+        int i = e % r, j = e / r;
+        Uh2[int64_t(t) * r * r + e] = i <= j ? Ur[i + int64_t(j) * m] : czero<C>();
+    }
+    // D <- Q_r^* D Q_r  (reflector k = 0 first, both sides)
+    for (int k = 0; k < r; ++k) {
+        const C* v = Ur + int64_t(k) * m;   // v_k = 1 implied, v_i = v[i] for i > k
+        C tau = taus[k];
+        for (int c = warp; c < m; c += nw) {   // left: columns
+            C* dc = Dw + int64_t(c) * m;
+            C w = lane == 0 ? dc[k] : czero<C>();
+            for (int i = k + 1 + lane; i < m; i += 32) gfmac(w, v[i], dc[i]);
+            w.x = warp_sum(w.x);
+            w.y = warp_sum(w.y);
+            C tw = gmulc(tau, w);
+            if (lane == 0) dc[k] = gsub(dc[k], tw);
+            for (int i = k + 1 + lane; i < m; i += 32) dc[i] = gsub(dc[i], gmul(v[i], tw));
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += bd) {   // right: rows
+            C w = Dw[i + int64_t(k) * m];
+            for (int j = k + 1; j < m; ++j) gfma(w, Dw[i + int64_t(j) * m], v[j]);
+            C tw = gmul(tau, w);
+            Dw[i + int64_t(k) * m] = gsub(Dw[i + int64_t(k) * m], tw);
+            for (int j = k + 1; j < m; ++j) Dw[i + int64_t(j) * m] = gsub(Dw[i + int64_t(j) * m], gmul(tw, gconj(v[j])));
+        }
+        __syncthreads();
+    }
+    // explicit Q_r = H_0 .. H_{r-1}
+    for (int64_t e = tid; e < mm; e += bd) Qr[e] = (e % m == e / m) ? mkc<C>(1, 0) : czero<C>();
+    __syncthreads();
+    for (int k = r - 1; k >= 0; --k) {
+        const C* v = Ur + int64_t(k) * m;
+        C tau = taus[k];
+        for (int c = warp; c < m; c += nw) {
+            C* qc = Qr + int64_t(c) * m;
+            C w = lane == 0 ? qc[k] : czero<C>();
+            for (int i = k + 1 + lane; i < m; i += 32) gfmac(w, v[i], qc[i]);
+            w.x = warp_sum(w.x);
+            w.y = warp_sum(w.y);
+            C tw = gmul(tau, w);
+            if (lane == 0) qc[k] = gsub(qc[k], tw);
+            for (int i = k + 1 + lane; i < m; i += 32) qc[i] = gsub(qc[i], gmul(v[i], tw));
+        }
+        __syncthreads();
+    }
+    // Cholesky of D-check_11 = Dw[r:, r:] (left-looking, lower, in place)
+    auto L = [&](int i, int j) -> C& { return Dw[(r + i) + int64_t(r + j) * m]; };
+    __shared__ R s_d;
+    for (int j = 0; j < n1; ++j) {
+        if (tid == 0) {
+            R d = L(j, j).x;
+            for (int k = 0; k < j; ++k) d -= gabs2(L(j, k));
+            if (!(d > R(0))) {
+                atomicExch(status, FIO_ENOTHPD);
+                d = R(1);
+            }
+            s_d = sqrt(d);
+        }
+        __syncthreads();
+        R dj = s_d;
+        for (int i = j + 1 + tid; i < n1; i += bd) {
+            C a = L(i, j);
+            for (int k = 0; k < j; ++k) a = gsub(a, gmul(L(i, k), gconj(L(j, k))));
+            L(i, j) = gscale(a, R(1) / dj);
+        }
+        __syncthreads();
+        if (tid == 0) L(j, j) = mkc<C>(dj, 0);
+        __syncthreads();
+    }
+    // D^_21 = D-check_21 L^{-*}: row i solves L conj(x) = conj(D-check_21[i, :])
+    for (int i = tid; i < r; i += bd) {
+        for (int j = 0; j < n1; ++j) {
+            C y = gconj(Dw[i + int64_t(r + j) * m]);
+            for (int k = 0; k < j; ++k) y = gsub(y, gmul(L(j, k), gconj(Dh21[i + int64_t(k) * r])));
+            Dh21[i + int64_t(j) * r] = gconj(gscale(y, R(1) / L(j, j).x));
+        }
+    }
+    __syncthreads();
+    // D^_22 = D-check_22 - D^_21 D^_21^*
+    for (int e = tid; e < r * r; e += bd) {
+        int i = e % r, j = e / r;
+        C a = Dw[i + int64_t(j) * m];
+        for (int k = 0; k < n1; ++k) a = gsub(a, gmul(Dh21[i + int64_t(k) * r], gconj(Dh21[j + int64_t(k) * r])));
+        Dh22[int64_t(t) * r * r + e] = a;
+    }
+    // A1 = L^{-1} Q1^*,  Q1 = Qr[:, r:]  (column c of A1: forward substitution)
+    for (int c = tid; c < m; c += bd) {
+        for (int j = 0; j < n1; ++j) {
+            C y = gconj(Qr[c + int64_t(r + j) * m]);
+            for (int k = 0; k < j; ++k) y = gsub(y, gmul(L(j, k), A1[k + int64_t(c) * m]));
+            A1[j + int64_t(c) * m] = gscale(y, R(1) / L(j, j).x);
+        }
+    }
+    __syncthreads();
+    // W = [A1; Q2^* - D^_21 A1]
+    float2* Wt = Wout + int64_t(t) * mm;
+    for (int64_t e = tid; e < mm; e += bd) {
+        int i = int(e % m), c = int(e / m);
+        C a;
+        if (i < n1) {
+            a = A1[i + int64_t(c) * m];
+        } else {
+            int ii = i - n1;
+            a = gconj(Qr[c + int64_t(ii) * m]);
+            for (int k = 0; k < n1; ++k) a = gsub(a, gmul(Dh21[ii + int64_t(k) * r], A1[k + int64_t(c) * m]));
+        }
+        Wt[e] = to_f2(a);
+    }
+}
+
+// Merge into the parent (Eq. 2.12).  Children have rank r; parent transfer
+// U_p is (2r x rp), float2.  Outputs D+ (2r x 2r) and U+ (2r x rp) in C.
+template <class C>
+__global__ void k_ulv_merge(const C* __restrict__ Dh22, const C* __restrict__ Uh2, const float2* __restrict__ B, int r,
+                            const float2* __restrict__ Up, int rp, C* __restrict__ Dplus, C* __restrict__ Uplus) {
+    const int t = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int m = 2 * r;
+    const C* D1 = Dh22 + int64_t(2 * t) * r * r;
+    const C* D2 = D1 + int64_t(r) * r;
+    const C* U1 = Uh2 + int64_t(2 * t) * r * r;
+    const C* U2 = U1 + int64_t(r) * r;
+    const float2* Bt = B + int64_t(t) * r * r;
+    C* Dp = Dplus + int64_t(t) * m * m;
+    // lower-left block: U2 B U1^*
+    for (int e = tid; e < m * m; e += bd) {
+        int i = e % m, j = e / m;
+        C a = czero<C>();
+        if (i < r && j < r) a = D1[i + j * r];
+        else if (i >= r && j >= r) a = D2[(i - r) + (j - r) * r];
+        else if (i >= r && j < r) {
+            // (U2 B U1^*)[i-r][j] = sum_p sum_q U2[i-r][p] B[p][q] conj(U1[j][q])
+            int ii = i - r;
+            for (int pp = 0; pp < r; ++pp) {
+                C bu = czero<C>();
+                for (int q = 0; q < r; ++q) gfma(bu, cvt<C>(Bt[pp + q * r]), gconj(U1[j + q * r]));
+                gfma(a, U2[ii + pp * r], bu);
+            }
+        } else {
+            // (U1 B^* U2^*)[i][j-r] = conj((U2 B U1^*)[j-r][i])
+            int jj = j - r;
+            C s = czero<C>();
+            for (int pp = 0; pp < r; ++pp) {
+                C bu = czero<C>();
+                for (int q = 0; q < r; ++q) gfma(bu, cvt<C>(Bt[pp + q * r]), gconj(U1[i + q * r]));
+                gfma(s, U2[jj + pp * r], bu);
+            }
+            a = gconj(s);
+        }
+        Dp[e] = a;
+    }
+    if (Up) {
+        const float2* Ut = Up + int64_t(t) * m * rp;
+        C* Upl = Uplus + int64_t(t) * m * rp;
+        for (int e = tid; e < m * rp; e += bd) {
+            int i = e % m, j = e / m;
+            const C* Ub = i < r ? U1 : U2;
+            int ii = i < r ? i : i - r, off = i < r ? 0 : r;
+            C a = czero<C>();
+            for (int q = 0; q < r; ++q) gfma(a, Ub[ii + q * r], cvt<C>(Ut[(off + q) + int64_t(j) * m]));
+            Upl[e] = a;
+        }
+    }
+}
+
+// Root: D+ = L L^*; Rinv = L^{-*} L^{-1} (complex64 column-major).
+__global__ void k_ulv_root(const double2* __restrict__ Dp, int m, float2* __restrict__ Rinv, double2* __restrict__ scr,
+                           int* status) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    double2* Lm = scr;               // m x m
+    double2* Li = scr + int64_t(m) * m;
+    for (int e = tid; e < m * m; e += bd) Lm[e] = Dp[e];
+    __syncthreads();
+    __shared__ double s_d;
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            double d = Lm[j + int64_t(j) * m].x;
+            for (int k = 0; k < j; ++k) d -= gabs2(Lm[j + int64_t(k) * m]);
+            if (!(d > 0)) {
+                atomicExch(status, FIO_ENOTHPD);
+                d = 1;
+            }
+            s_d = sqrt(d);
+        }
+        __syncthreads();
+        double dj = s_d;
+        for (int i = j + 1 + tid; i < m; i += bd) {
+            double2 a = Lm[i + int64_t(j) * m];
+            for (int k = 0; k < j; ++k) a = gsub(a, gmul(Lm[i + int64_t(k) * m], gconj(Lm[j + int64_t(k) * m])));
+            Lm[i + int64_t(j) * m] = gscale(a, 1.0 / dj);
+        }
+        __syncthreads();
+        if (tid == 0) Lm[j + int64_t(j) * m] = make_double2(dj, 0);
+        __syncthreads();
+    }
+    // Li = L^{-1}, column by column
+    for (int c = tid; c < m; c += bd)
+        for (int j = 0; j < m; ++j) {
+            double2 y = make_double2(j == c ? 1.0 : 0.0, 0);
+            for (int k = c; k < j; ++k) y = gsub(y, gmul(Lm[j + int64_t(k) * m], Li[k + int64_t(c) * m]));
+            Li[j + int64_t(c) * m] = (j < c) ? make_double2(0, 0) : gscale(y, 1.0 / Lm[j + int64_t(j) * m].x);
+        }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += bd) {
+        int i = e % m, j = e / m;
+        double2 a = make_double2(0, 0);
+        for (int k = max(i, j); k < m; ++k) gfmac(a, Li[k + int64_t(i) * m], Li[k + int64_t(j) * m]);
+        Rinv[e] = make_float2(float(a.x), float(a.y));
+    }
+}
+
+template <class C> __global__ void k_to_f64(const C* __restrict__ a, double2* __restrict__ b, int64_t n) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_double2(double(a[e].x), double(a[e].y));
+}
+
+// ------------------------------------------------------------- solve
+// up:  z = W_t y_t;  rows < m-r -> bh1 (rows t*(m-r)), rows >= m-r -> ynext (rows t*r)
+__global__ void k_ulv_up(const float2* __restrict__ W, int64_t nodes, int m, int r, const float2* __restrict__ y,
+                         int64_t ldy, float2* __restrict__ bh1, int64_t ldb, float2* __restrict__ ynext, int64_t ldn) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= nodes * m) return;
+    int col = blockIdx.y;
+    int64_t t = e / m;
+    int i = int(e % m);
+    const float2* Wt = W + t * m * m;
+    const float2* yt = y + col * ldy + t * m;
+    float2 a = make_float2(0.f, 0.f);
+    for (int j = 0; j < m; ++j) cfma(a, Wt[i + int64_t(j) * m], yt[j]);
+    const int n1 = m - r;
+    if (i < n1) bh1[col * ldb + t * n1 + i] = a;
+    else ynext[col * ldn + t * r + (i - n1)] = a;
+}
+
+// down: c_t = W_t^* [bh1_t; c2_t],  c2_t = cpar rows t*r..
+__global__ void k_ulv_down(const float2* __restrict__ W, int64_t nodes, int m, int r, const float2* __restrict__ bh1,
+                           int64_t ldb, const float2* __restrict__ cpar, int64_t ldp, float2* __restrict__ out,
+                           int64_t ldo) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= nodes * m) return;
+    int col = blockIdx.y;
+    int64_t t = e / m;
+    int c = int(e % m);
+    const int n1 = m - r;
+    const float2* Wc = W + t * m * m + int64_t(c) * m;
+    const float2* b = bh1 + col * ldb + t * n1;
+    const float2* p = cpar + col * ldp + t * r;
+    float2 a = make_float2(0.f, 0.f);
+    for (int i = 0; i < n1; ++i) cfmac(a, Wc[i], b[i]);
+    for (int i = 0; i < r; ++i) cfmac(a, Wc[n1 + i], p[i]);
+    out[col * ldo + e] = a;
+}
+
+__global__ void k_gemv_sq(const float2* __restrict__ A, int m, const float2* __restrict__ x, int64_t ldx,
+                          float2* __restrict__ y, int64_t ldy) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int col = blockIdx.y;
+    if (i >= m) return;
+    float2 a = make_float2(0.f, 0.f);
+    for (int j = 0; j < m; ++j) cfma(a, A[i + int64_t(j) * m], x[col * ldx + j]);
+    y[col * ldy + i] = a;
+}
+
+template <class C>
+fio_status factor_level(fio_hss* h, int l, const C* Dc, const C* Uc, DevBuf& scr, DevBuf& dh22, DevBuf& uh2,
+                        int* d_status, cudaStream_t st) {
+    const int nn = 1 << l, m = h->m(l), r = h->ranks[l];
+    const int64_t per = 3 * int64_t(m) * m + 2 * int64_t(m) * r + r;
+    FIO_TRY(scr.ensure(size_t(nn) * per * sizeof(C)));
+    FIO_TRY(dh22.ensure(std::max<size_t>(16, size_t(nn) * r * r * sizeof(C))));
+    FIO_TRY(uh2.ensure(std::max<size_t>(16, size_t(nn) * r * r * sizeof(C))));
+    FIO_TRY(h->W[l].ensure(size_t(nn) * m * m * 8));
+    const float2* Df = (l == h->Lh) ? h->D.as<float2>() : nullptr;
+    const float2* Uf = (l == h->Lh) ? h->U[l].as<float2>() : nullptr;
+    k_ulv_node<C><<<nn, TB, 0, st>>>(Df, Dc, Uf, Uc, m, r, h->W[l].as<float2>(), dh22.as<C>(), uh2.as<C>(), scr.as<C>(),
+                                     d_status);
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+}  // namespace
+}  // namespace fio
+
+using namespace fio;
+
+extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
+    if (!h) return fail(FIO_EINVAL, "hss_ulv_factor: null handle");
+    cudaStream_t st = as_stream(stream);
+    const int Lh = h->Lh;
+    DevBuf scr, dh22[2], uh2[2], dplus, uplus, dconv, stat;
+    auto release = [&]() {
+        for (DevBuf* b : {&scr, &dh22[0], &dh22[1], &uh2[0], &uh2[1], &dplus, &uplus, &dconv, &stat}) b->release();
+    };
+    fio_status s;
+    if ((s = stat.ensure(4)) != FIO_OK) return s;
+    FIO_CUDA(cudaMemsetAsync(stat.p, 0, 4, st));
+    int* d_status = stat.as<int>();
+    bool cur_f64 = false;
+    for (int l = Lh; l >= 1; --l) {
+        const int nn = 1 << l;
+        const bool f64 = nn <= kFp64Nodes;
+        const int r = h->ranks[l];
+        int cur = l & 1;
+        // inputs of this level: leaf generators, or D+/U+ of the merge (in dplus/uplus)
+        if (l == Lh) {
+            s = f64 ? factor_level<double2>(h, l, nullptr, nullptr, scr, dh22[cur], uh2[cur], d_status, st)
+                    : factor_level<float2>(h, l, nullptr, nullptr, scr, dh22[cur], uh2[cur], d_status, st);
+        } else if (f64 && !cur_f64) {
+            // promote the merged blocks to FP64
+            int64_t nD = int64_t(nn) * h->m(l) * h->m(l), nU = int64_t(nn) * h->m(l) * r;
+            if ((s = dconv.ensure(size_t(nD + nU) * 16 + 16)) != FIO_OK) { release(); return s; }
+            double2* D64 = dconv.as<double2>();
+            double2* U64 = D64 + nD;
+            if (nD) k_to_f64<float2><<<cdiv(nD, TB), TB, 0, st>>>(dplus.as<float2>(), D64, nD);
+            if (nU) k_to_f64<float2><<<cdiv(nU, TB), TB, 0, st>>>(uplus.as<float2>(), U64, nU);
+            s = factor_level<double2>(h, l, D64, U64, scr, dh22[cur], uh2[cur], d_status, st);
+        } else if (f64) {
+            s = factor_level<double2>(h, l, dplus.as<double2>(), uplus.as<double2>(), scr, dh22[cur], uh2[cur], d_status, st);
+        } else {
+            s = factor_level<float2>(h, l, dplus.as<float2>(), uplus.as<float2>(), scr, dh22[cur], uh2[cur], d_status, st);
+        }
+        if (s != FIO_OK) { release(); return s; }
+        // merge into level l-1
+        const int np = nn / 2, mp = 2 * r, rp = h->ranks[l - 1];
+        const float2* Up = (l - 1 >= 1) ? h->U[l - 1].as<float2>() : nullptr;
+        size_t es = f64 ? 16 : 8;
+        DevBuf tmpD, tmpU;
+        if ((s = tmpD.ensure(std::max<size_t>(16, size_t(np) * mp * mp * es))) != FIO_OK) { release(); return s; }
+        if ((s = tmpU.ensure(std::max<size_t>(16, size_t(np) * mp * std::max(rp, 1) * es))) != FIO_OK) {
+            tmpD.release();
+            release();
+            return s;
+        }
+        if (mp > 0) {
+            if (f64)
+                k_ulv_merge<double2><<<np, TB, 0, st>>>(dh22[cur].as<double2>(), uh2[cur].as<double2>(), h->B[l - 1].as<float2>(),
+                                                        r, Up, rp, tmpD.as<double2>(), tmpU.as<double2>());
+            else
+                k_ulv_merge<float2><<<np, TB, 0, st>>>(dh22[cur].as<float2>(), uh2[cur].as<float2>(), h->B[l - 1].as<float2>(),
+                                                       r, Up, rp, tmpD.as<float2>(), tmpU.as<float2>());
+        }
+        cudaError_t e = cudaStreamSynchronize(st);   // the scratch buffers are reused next level
+        dplus.release();
+        uplus.release();
+        dplus = tmpD;
+        uplus = tmpU;
+        cur_f64 = f64;
+        if (e != cudaSuccess) { release(); return cuda_status(e, "hss_ulv_factor: level"); }
+    }
+    // root
+    const int m0 = 2 * h->ranks[1];
+    if ((s = h->Rinv.ensure(std::max<size_t>(8, size_t(m0) * m0 * 8))) != FIO_OK) { release(); return s; }
+    if (m0 > 0) {
+        if ((s = scr.ensure(size_t(2) * m0 * m0 * 16)) != FIO_OK) { release(); return s; }
+        const double2* D64 = dplus.as<double2>();
+        if (!cur_f64) {
+            if ((s = dconv.ensure(size_t(m0) * m0 * 16)) != FIO_OK) { release(); return s; }
+            k_to_f64<float2><<<cdiv(int64_t(m0) * m0, TB), TB, 0, st>>>(dplus.as<float2>(), dconv.as<double2>(),
+                                                                        int64_t(m0) * m0);
+            D64 = dconv.as<double2>();
+        }
+        k_ulv_root<<<1, TB, 0, st>>>(D64, m0, h->Rinv.as<float2>(), scr.as<double2>(), d_status);
+    }
+    int hst = 0;
+    cudaMemcpyAsync(&hst, d_status, 4, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_status(e, "hss_ulv_factor");
+    if (hst == FIO_ENOTHPD) return fail(FIO_ENOTHPD, "hss_ulv_factor: Cholesky pivot <= 0 (G~ not HPD)");
+    h->factored = true;
+    return FIO_OK;
+}
+
+extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int64_t ld, int k, void* stream) {
+    if (!hc) return fail(FIO_EINVAL, "hss_solve: null handle");
+    if (!hc->factored) return fail(FIO_EINVAL, "hss_solve: call hss_ulv_factor first");
+    if (k < 0 || ld < hc->N) return fail(FIO_EINVAL, "hss_solve: need k >= 0 and ld >= N");
+    if (k == 0) return FIO_OK;
+    fio_hss* h = const_cast<fio_hss*>(hc);
+    cudaStream_t st = as_stream(stream);
+    const int Lh = h->Lh;
+    // per level: bh1_l (2^l (m_l - r_l)), y_l (rows(l), l < Lh), c_l (rows(l), l < Lh)
+    std::vector<int64_t> ob(Lh + 1), oy(Lh + 1), oc(Lh + 1);
+    int64_t tot = 0;
+    for (int l = 0; l <= Lh; ++l) {
+        ob[l] = tot;
+        tot += (l >= 1) ? (int64_t(1) << l) * (h->m(l) - h->ranks[l]) : 0;
+        oy[l] = tot;
+        tot += (l < Lh) ? h->rows(l) : 0;
+        oc[l] = tot;
+        tot += (l < Lh) ? h->rows(l) : 0;
+    }
+    FIO_TRY(h->solve_ws.ensure(std::max<size_t>(16, size_t(tot) * k * 8)));
+    float2* w = h->solve_ws.as<float2>();
+    auto bh = [&](int l) { return w + ob[l] * k; };
+    auto yv = [&](int l) { return w + oy[l] * k; };
+    auto cv = [&](int l) { return w + oc[l] * k; };
+    const float2* B = static_cast<const float2*>(Bv);
+    float2* X = static_cast<float2*>(Xv);
+    for (int l = Lh; l >= 1; --l) {
+        const int m = h->m(l), r = h->ranks[l];
+        const float2* in = (l == Lh) ? B : yv(l);
+        int64_t ldin = (l == Lh) ? ld : h->rows(l);
+        int64_t nb = (int64_t(1) << l) * (m - r);
+        dim3 g(cdiv((int64_t(1) << l) * m, TB), k);
+        FIO_LAUNCH("k_ulv_up", st,
+                   k_ulv_up<<<g, TB, 0, st>>>(h->W[l].as<float2>(), int64_t(1) << l, m, r, in, ldin, bh(l),
+                                              std::max<int64_t>(nb, 1), yv(l - 1), std::max<int64_t>(h->rows(l - 1), 1)));
+    }
+    const int m0 = 2 * h->ranks[1];
+    if (m0 > 0) {
+        dim3 g(cdiv(m0, TB), k);
+        FIO_LAUNCH("k_ulv_root", st, k_gemv_sq<<<g, TB, 0, st>>>(h->Rinv.as<float2>(), m0, yv(0), m0, cv(0), m0));
+    }
+    for (int l = 1; l <= Lh; ++l) {
+        const int m = h->m(l), r = h->ranks[l];
+        float2* out = (l == Lh) ? X : cv(l);
+        int64_t ldo = (l == Lh) ? ld : h->rows(l);
+        int64_t nb = (int64_t(1) << l) * (m - r);
+        dim3 g(cdiv((int64_t(1) << l) * m, TB), k);
+        FIO_LAUNCH("k_ulv_down", st,
+                   k_ulv_down<<<g, TB, 0, st>>>(h->W[l].as<float2>(), int64_t(1) << l, m, r, bh(l),
+                                                std::max<int64_t>(nb, 1), cv(l - 1),
+                                                std::max<int64_t>(h->rows(l - 1), 1), out, ldo));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
