@@ -127,6 +127,13 @@ def kernel_bytes(name, N, r, kc, binfo, hinfo):
         return 2 * S + tables_quad
     if name.startswith("k_M"):
         return 2 * S + N * r * r * 8
+    nB, nC = binfo["sU"] - binfo["h"], binfo["h"] - binfo["sV"]
+    if name.startswith("k_bf_left"):     # U^(*) + B^(*) levels + (M^* for the adjoint) ; middle state
+        b = vec + N * lsU * 8 + nB * tables_quad + S
+        return b + (N * r * r * 8 if name.endswith("adj") else 0)
+    if name.startswith("k_bf_right"):    # V^(*) + C^(*) levels + (M for the forward) ; middle state
+        b = vec + nVP + nC * tables_quad + S
+        return b + (N * r * r * 8 if name.endswith("fwd") else 0)
     if name in ("k_ulv_up", "k_ulv_down"):
         # average over the Lh launches of one pass: W_l plus the level's vectors
         Lh, leaf, ranks = hinfo["Lh"], hinfo["leaf"], hinfo["ranks"]

@@ -96,6 +96,12 @@ fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, f
  *   Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA. */
 fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream);
 
+/* bf_set_path -- choose the kernels of bf_apply (no paper counterpart; the
+ *   results agree to FP32 rounding):  0 = automatic (fused two-pass kernels
+ *   where r = 16 and n >= 64, else per-level kernels), 1 = one kernel per
+ *   factor (per-level), 2 = fused two-pass (FIO_EINVAL where unsupported). */
+fio_status bf_set_path(fio_bf* bf, int path);
+
 /* bf_info -- sizes of a handle: out[0..7] = n, d, r, L, h, sU (space level of
  *   U), sV (space level of V), bytes of device factor tables. */
 fio_status bf_info(const fio_bf* bf, int64_t* out8);

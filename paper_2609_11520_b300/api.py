@@ -47,6 +47,11 @@ class BF:
     def handle(self):
         return self._h
 
+    def set_path(self, path):
+        """0 automatic, 1 per-level kernels, 2 fused two-pass kernels."""
+        check(lib.bf_set_path(self._h, int({"auto": 0, "per_level": 1, "fused": 2}.get(path, path))))
+        return self
+
     def info(self):
         o = (ctypes.c_int64 * 8)()
         check(lib.bf_info(self._h, o))

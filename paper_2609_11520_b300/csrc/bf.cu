@@ -62,17 +62,24 @@ __global__ void k_tab_UP(float2* UP, PhaseDev ph, int n, int L, int sU) {
     UP[e] = expi2pi(phi(ph, double(i) / n, freq_center(n, L - sU, b)));
 }
 
-// F_s[q][c][beta][t], quad q = (tau at space level s, b' at frequency level L-s-1).
-__global__ void k_tab_F(float2* F, PhaseDev ph, Cheb ch, int n, int L, int s, int r) {
+// F_s[q][c][beta][t], quad (tau at space level s, b' at frequency level L-s-1)
+// stored at q = box 2^(h-1) + tau 2^(h-s-1) + (b' mod 2^(h-s-1)), box = the
+// frequency box of level L-h holding b' (contiguous per box for the fused apply).
+__device__ __forceinline__ int64_t fquad(int64_t tau, int64_t bq, int h, int s) {
+    int64_t box = bq >> (h - s - 1), sl = bq & ((int64_t(1) << (h - s - 1)) - 1);
+    return (box << (h - 1)) + (tau << (h - s - 1)) + sl;
+}
+
+__global__ void k_tab_F(float2* F, PhaseDev ph, Cheb ch, int n, int L, int h, int s, int r) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t nquad = int64_t(n) / 2;
     if (e >= nquad * 4 * r) return;
     int t = int(e % r);
     int64_t rest = e / r;
     int be = int(rest & 1), c = int((rest >> 1) & 1);
-    int64_t q = rest >> 2;
-    int64_t nbq = int64_t(1) << (L - s - 1);
-    int64_t tau = q / nbq, bq = q % nbq;
+    int64_t qR = rest >> 2;
+    int64_t box = qR >> (h - 1), rem = qR & ((int64_t(1) << (h - 1)) - 1);
+    int64_t tau = rem >> (h - s - 1), bq = (box << (h - s - 1)) + (rem & ((int64_t(1) << (h - s - 1)) - 1));
     double g = freq_node(ch, n, L - s, 2 * bq + be, t);
     double yc = space_center(s + 1, 2 * tau + c), yp = space_center(s, tau);
     F[e] = expi2pi(phi(ph, yc, g) - phi(ph, yp, g));
@@ -232,11 +239,21 @@ __global__ void k_M(const float2* __restrict__ Sin, float2* __restrict__ Sout, c
 //  Adjoint: the reverse.
 template <bool MS, bool ADJ>
 __global__ void k_quad(const float2* __restrict__ Sin, float2* __restrict__ Sout, const float2* __restrict__ T,
-                       const float* __restrict__ Pc, int n, int L, int s, int r) {
+                       const float* __restrict__ Pc, int n, int L, int h, int s, int r) {
+    // MS lanes read row i of Pc[o] across t, SM lanes read column j of Pc[e]
+    // across t: store Pc so that the lanes of a warp hit consecutive banks
+    // (MS: transposed, sPc[o][t][i]; SM: as is, sPc[e][t][j]).
     __shared__ float sPc[2 * kMaxR * kMaxR];
     __shared__ float2 sx[8][2 * kMaxR];
     __shared__ float2 sg[8][4 * kMaxR];
-    for (int e = threadIdx.x; e < 2 * r * r; e += blockDim.x) sPc[e] = Pc[e];
+    for (int e = threadIdx.x; e < 2 * r * r; e += blockDim.x) {
+        if (MS) {
+            int c = e / (r * r), rem = e % (r * r), t = rem / r, i = rem % r;
+            sPc[e] = Pc[(c * r + i) * r + t];
+        } else {
+            sPc[e] = Pc[e];
+        }
+    }
     __syncthreads();
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t q = int64_t(blockIdx.x) * 8 + w;
@@ -260,15 +277,17 @@ __global__ void k_quad(const float2* __restrict__ Sin, float2* __restrict__ Sout
     }
     if (act) sx[w][hl * r + idx] = in[pin * r + idx];
     __syncwarp();
-    const float2* tq = T + q * 4 * r;
+    // C levels (forward SM / adjoint MS) use the box-ordered F layout
+    const int64_t qt = (MS == ADJ) ? fquad(tau, bq, h, s) : q;
+    const float2* tq = T + qt * 4 * r;
     float2 y = make_float2(0.f, 0.f);
     if (MS) {
         // lane = (o = hl, i = idx)
         if (act) {
-            const float* P = sPc + hl * r * r + idx * r;
+            const float* P = sPc + hl * r * r + idx;
             float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
             for (int t = 0; t < r; ++t) {
-                float pv = P[t];
+                float pv = P[t * r];
                 float2 x0 = sx[w][t], x1 = sx[w][r + t];
                 h0.x = fmaf(pv, x0.x, h0.x); h0.y = fmaf(pv, x0.y, h0.y);
                 h1.x = fmaf(pv, x1.x, h1.x); h1.y = fmaf(pv, x1.y, h1.y);
@@ -335,26 +354,26 @@ fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t l
     if (!adjoint) {
         FIO_LAUNCH("k_V_fwd", st, k_V_fwd<<<gNr, TB, shV, st>>>(X, ld, a, bf->VP.as<float2>(), PV, n, L, bf->sV, r));
         for (int s = bf->sV; s < bf->h; ++s) {
-            FIO_LAUNCH("k_quad_C_fwd", st, k_quad<false, false><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, s, r));
+            FIO_LAUNCH("k_quad_C_fwd", st, k_quad<false, false><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, bf->h, s, r));
             std::swap(a, b);
         }
         FIO_LAUNCH("k_M_fwd", st, k_M<false><<<gNr, TB, 0, st>>>(a, b, bf->M.as<float2>(), n, r));
         std::swap(a, b);
         for (int s = bf->h; s < bf->sU; ++s) {
-            FIO_LAUNCH("k_quad_B_fwd", st, k_quad<true, false><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, s, r));
+            FIO_LAUNCH("k_quad_B_fwd", st, k_quad<true, false><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, bf->h, s, r));
             std::swap(a, b);
         }
         FIO_LAUNCH("k_U_fwd", st, k_U_fwd<<<gN, TB, shU, st>>>(a, Y, ld, bf->UP.as<float2>(), PU, n, L, bf->sU, r));
     } else {
         FIO_LAUNCH("k_U_adj", st, k_U_adj<<<gNr, TB, shU, st>>>(X, ld, a, bf->UP.as<float2>(), PU, n, L, bf->sU, r));
         for (int s = bf->sU - 1; s >= bf->h; --s) {
-            FIO_LAUNCH("k_quad_B_adj", st, k_quad<false, true><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, s, r));
+            FIO_LAUNCH("k_quad_B_adj", st, k_quad<false, true><<<gQ, TB, 0, st>>>(a, b, bf->B[s - bf->h].as<float2>(), Pc, n, L, bf->h, s, r));
             std::swap(a, b);
         }
         FIO_LAUNCH("k_M_adj", st, k_M<true><<<gNr, TB, 0, st>>>(a, b, bf->M.as<float2>(), n, r));
         std::swap(a, b);
         for (int s = bf->h - 1; s >= bf->sV; --s) {
-            FIO_LAUNCH("k_quad_C_adj", st, k_quad<true, true><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, s, r));
+            FIO_LAUNCH("k_quad_C_adj", st, k_quad<true, true><<<gQ, TB, 0, st>>>(a, b, bf->C[s - bf->sV].as<float2>(), Pc, n, L, bf->h, s, r));
             std::swap(a, b);
         }
         FIO_LAUNCH("k_V_adj", st, k_V_adj<<<gN, TB, shV, st>>>(a, Y, ld, bf->VP.as<float2>(), PV, n, L, bf->sV, r));
@@ -416,7 +435,7 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
     bf->C.resize(bf->h - bf->sV);
     for (int lv = bf->sV; lv < bf->h; ++lv) {
         if ((s = bf->C[lv - bf->sV].ensure(nT * 8)) != FIO_OK) return cleanup(s);
-        k_tab_F<<<cdiv(nT, TB), TB, 0, st>>>(bf->C[lv - bf->sV].as<float2>(), ph, ch, n, L, lv, r);
+        k_tab_F<<<cdiv(nT, TB), TB, 0, st>>>(bf->C[lv - bf->sV].as<float2>(), ph, ch, n, L, bf->h, lv, r);
     }
     bf->B.resize(bf->sU - bf->h);
     for (int lv = bf->h; lv < bf->sU; ++lv) {
@@ -437,17 +456,28 @@ extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, i
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
     const int64_t stateN = int64_t(bf->n) * bf->r;
+    cudaStream_t st = as_stream(stream);
+    const bool fused = bf_fused_ok(bf) && !bf->force_unfused;
     // column chunk: at most 64 columns or 1 GiB of state, whichever is smaller
-    int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(1) << 30) / (2 * stateN * 8)))));
-    FIO_TRY(bf->ws.ensure(size_t(2) * stateN * kc * 8));
+    const int nstate = fused ? 1 : 2;
+    int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(1) << 30) / (nstate * stateN * 8)))));
+    FIO_TRY(bf->ws.ensure(size_t(nstate) * stateN * kc * 8));
     float2* s0 = bf->ws.as<float2>();
     float2* s1 = s0 + stateN * kc;
-    cudaStream_t st = as_stream(stream);
     for (int c0 = 0; c0 < k; c0 += kc) {
         int cc = std::min(kc, k - c0);
-        FIO_TRY(bf_apply_cols(bf, reinterpret_cast<const float2*>(X) + c0 * ld, reinterpret_cast<float2*>(Y) + c0 * ld,
-                              ld, cc, adjoint, s0, s1, st));
+        const float2* Xc = reinterpret_cast<const float2*>(X) + c0 * ld;
+        float2* Yc = reinterpret_cast<float2*>(Y) + c0 * ld;
+        if (fused) FIO_TRY(bf_apply_fused(bf, Xc, Yc, ld, cc, adjoint, s0, st));
+        else FIO_TRY(bf_apply_cols(bf, Xc, Yc, ld, cc, adjoint, s0, s1, st));
     }
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
+    if (!bf || path < 0 || path > 2) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
+    if (path == 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
+    bf->force_unfused = (path == 1);
     return FIO_OK;
 }
 

@@ -12,6 +12,7 @@
 // Tables (complex64):
 //   VP[a][j]        e^{2 pi i Phi(y_a, xi_j)}            a: space box of level sV
 //   F_s[q][c][b][t] e^{2 pi i (Phi(y_tau', gamma_bt) - Phi(y_tau, gamma_bt))}   C level s
+//                   (quads ordered by the frequency box of level L-h that holds them)
 //   M[p][i][j]      e^{2 pi i (Phi(z_i, gamma_j) - Phi(z_i, eta) - Phi(y, gamma_j))}
 //   E_s[q][c][b][i] e^{2 pi i (Phi(z_tau_i, eta_beta) - Phi(z_tau_i, eta_sigma))} B level s
 //   UP[x][b]        e^{2 pi i Phi(x, eta_b)}              b: frequency box of level L-sU
@@ -33,6 +34,7 @@ struct fio_bf {
     std::vector<fio::DevBuf> B;    // index s - h
     fio::DevBuf ws;                // two coefficient states
     int64_t table_bytes = 0;
+    bool force_unfused = false;    // use the per-level kernels even where the fused pass applies
     int64_t N() const { return int64_t(n); }
     size_t pv_off() const { return 0; }
     size_t pu_off() const { return size_t(lsV) * r; }
@@ -40,6 +42,11 @@ struct fio_bf {
 };
 
 namespace fio {
+// Fused two-pass apply (r = 16, L >= 6): middle state `mid` of N*r*kc complex.
+bool bf_fused_ok(const fio_bf* bf);
+int bf_fused_kc(const fio_bf* bf);
+fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, float2* mid,
+                          cudaStream_t st);
 // Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st);

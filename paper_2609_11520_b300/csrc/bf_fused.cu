@@ -1,0 +1,504 @@
+// Fused two-pass butterfly apply (r = 16), the B300 form of Eq. 2.1.
+//
+// The butterfly splits at the middle level h into two independent halves:
+//   left half  (space side):     U, B^[h+1..T]  -- one CTA per space box tau_h
+//                                (2^(L-h) pairs, all frequency boxes sigma)
+//   right half (frequency side): C^[h+1..T], V  -- one CTA per frequency box
+//                                sigma_h (2^h pairs, all space boxes tau)
+// K~^* x: left half (U^*, B^*, M^*) -> middle state -> right half (C^*, V^*).
+// K~ x:   right half (V, C, M)      -> middle state -> left half (B, U).
+// Inside a CTA the coefficient state of KC columns stays in shared memory;
+// only the input vectors, the middle state (N r complex per column) and the
+// output vectors cross HBM, and every factor table is read once per CTA.
+//
+// In-place transfer levels: a quad (two input pairs -> two output pairs)
+// keeps the two physical slots of its inputs for its outputs.  A pair's
+// physical slot is then a partial bit reversal of its logical index; for a
+// half with W = number of free frequency (left) / space (right) bits at level
+// s and j transfer levels between s and the half's outer end:
+//   phys_s(a, b) = a 2^W + rev_j(b mod 2^j) 2^(W-j) + (b >> j),
+// and the quad of level s acts on the slot pair {base, base + 2^(W-1)} with
+//   base = a 2^W + rev_(j-1)(s' mod 2^(j-1)) 2^(W-j) + (s' >> (j-1)).
+// Threads enumerate quads by physical slot, so that consecutive threads touch
+// consecutive slots, and shared memory is XOR-swizzled in 16-byte chunks.
+#include "bf.cuh"
+
+namespace fio {
+namespace {
+
+constexpr int R = 16;
+// Pc[c] blocks in shared memory are PCS floats apart: the two blocks that the
+// lanes of a warp read together fall into different banks.
+constexpr int PCS = R * R + 4;
+
+struct Tabs {
+    const float2* t[24];
+};
+
+__device__ __forceinline__ int rev_bits(int x, int bits) { return bits > 0 ? int(__brev(unsigned(x)) >> (32 - bits)) : 0; }
+
+// float2 offset of coefficient i of physical pair slot p (16-byte chunks XOR-swizzled)
+__device__ __forceinline__ int sw(int p, int i) { return p * R + ((((i >> 1) ^ (p & 7)) << 1) | (i & 1)); }
+
+__device__ __forceinline__ void load_pair(const float2* S, int p, float2 (&x)[R]) {
+#pragma unroll
+    for (int m = 0; m < R / 2; ++m) {
+        float4 v = *reinterpret_cast<const float4*>(S + p * R + ((m ^ (p & 7)) << 1));
+        x[2 * m] = make_float2(v.x, v.y);
+        x[2 * m + 1] = make_float2(v.z, v.w);
+    }
+}
+__device__ __forceinline__ void store_pair(float2* S, int p, const float2 (&y)[R]) {
+#pragma unroll
+    for (int m = 0; m < R / 2; ++m)
+        *reinterpret_cast<float4*>(S + p * R + ((m ^ (p & 7)) << 1)) =
+            make_float4(y[2 * m].x, y[2 * m].y, y[2 * m + 1].x, y[2 * m + 1].y);
+}
+__device__ __forceinline__ void load_row(const float2* __restrict__ g, float2 (&v)[R]) {
+#pragma unroll
+    for (int m = 0; m < R / 2; ++m) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(g) + m);
+        v[2 * m] = make_float2(a.x, a.y);
+        v[2 * m + 1] = make_float2(a.z, a.w);
+    }
+}
+
+// One transfer level of a half on KC columns of in-place state.
+//   MS ("mix, then scale"):  y[o][i] = sum_e Phi(o,e,i) sum_t Pc[o][i][t] x[e][t]
+//   SM ("scale, then mix"):  y[o][j] = sum_e sum_t Pc[e][t][j] Phi(o,e,t) x[e][t]
+//   Phi(o,e,.) = T[q][o][e][.] (forward) or conj(T[q][e][o][.]) (adjoint).
+// LEFT selects the slot/table geometry of the space-side half.
+template <int KC, bool LEFT, bool MS, bool ADJ>
+__device__ void level_op(float2* S, int P, const float* sPc, const float2* __restrict__ T, int box, int s, int L,
+                         int h, int sU) {
+    const int W = LEFT ? L - s : h - s;
+    const int j = LEFT ? sU - s : h - s;
+    const int half = 1 << (W - 1);
+    const int ntask = P * KC;
+    for (int b0 = 0; b0 < ntask; b0 += blockDim.x) {
+        const int id = b0 + threadIdx.x;
+        const bool act = id < ntask;
+        int col = 0, o = 0, base = 0;
+        int64_t q = 0;
+        float2 x0[R], x1[R];
+        if (act) {
+            col = id / P;
+            const int rem = id - col * P;
+            const int qi = rem >> 1;
+            o = rem & 1;
+            const int a = qi >> (W - 1), rr = qi & (half - 1);
+            base = (a << W) | rr;
+            if (LEFT) {
+                const int wj = W - j;   // = L - sU
+                const int sg = ((rr & ((1 << wj) - 1)) << (j - 1)) | rev_bits(rr >> wj, j - 1);
+                q = ((int64_t(box) << (s - h)) + a) * (int64_t(1) << (L - s - 1)) + sg;
+            } else {
+                const int sl = rev_bits(rr, W - 1);
+                q = (int64_t(box) << (h - 1)) + (int64_t(a) << (h - s - 1)) + sl;
+            }
+            const float2* Sc = S + col * P * R;
+            load_pair(Sc, base, x0);
+            load_pair(Sc, base + half, x1);
+        }
+        __syncwarp();
+        if (act) {
+            float2* Sc = S + col * P * R;
+            float2 y[R];
+            const float2* tq = T + q * 4 * R;
+            if (MS) {
+                float2 ph0[R], ph1[R];
+                if (!ADJ) {
+                    load_row(tq + (o * 2 + 0) * R, ph0);
+                    load_row(tq + (o * 2 + 1) * R, ph1);
+                } else {
+                    load_row(tq + (0 * 2 + o) * R, ph0);
+                    load_row(tq + (1 * 2 + o) * R, ph1);
+                }
+                const float* Po = sPc + o * PCS;
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int t4 = 0; t4 < R / 4; ++t4) {
+                        float4 pv = *reinterpret_cast<const float4*>(Po + i * R + 4 * t4);
+                        float pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int t = 4 * t4 + u;
+                            h0.x = fmaf(pp[u], x0[t].x, h0.x);
+                            h0.y = fmaf(pp[u], x0[t].y, h0.y);
+                            h1.x = fmaf(pp[u], x1[t].x, h1.x);
+                            h1.y = fmaf(pp[u], x1[t].y, h1.y);
+                        }
+                    }
+                    float2 acc = make_float2(0.f, 0.f);
+                    if (!ADJ) {
+                        cfma(acc, ph0[i], h0);
+                        cfma(acc, ph1[i], h1);
+                    } else {
+                        cfmac(acc, ph0[i], h0);
+                        cfmac(acc, ph1[i], h1);
+                    }
+                    y[i] = acc;
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float2 ph[R];
+                    if (!ADJ) load_row(tq + (o * 2 + e) * R, ph);
+                    else load_row(tq + (e * 2 + o) * R, ph);
+                    const float* Pe = sPc + e * PCS;
+#pragma unroll
+                    for (int t = 0; t < R; ++t) {
+                        const float2 xv = e ? x1[t] : x0[t];
+                        const float2 g = ADJ ? cmulc(ph[t], xv) : cmul(ph[t], xv);
+#pragma unroll
+                        for (int j4 = 0; j4 < R / 4; ++j4) {
+                            float4 pv = *reinterpret_cast<const float4*>(Pe + t * R + 4 * j4);
+                            y[4 * j4 + 0].x = fmaf(pv.x, g.x, y[4 * j4 + 0].x);
+                            y[4 * j4 + 0].y = fmaf(pv.x, g.y, y[4 * j4 + 0].y);
+                            y[4 * j4 + 1].x = fmaf(pv.y, g.x, y[4 * j4 + 1].x);
+                            y[4 * j4 + 1].y = fmaf(pv.y, g.y, y[4 * j4 + 1].y);
+                            y[4 * j4 + 2].x = fmaf(pv.z, g.x, y[4 * j4 + 2].x);
+                            y[4 * j4 + 2].y = fmaf(pv.z, g.y, y[4 * j4 + 2].y);
+                            y[4 * j4 + 3].x = fmaf(pv.w, g.x, y[4 * j4 + 3].x);
+                            y[4 * j4 + 3].y = fmaf(pv.w, g.y, y[4 * j4 + 3].y);
+                        }
+                    }
+                }
+            }
+            store_pair(Sc, o ? base + half : base, y);
+        }
+    }
+    __syncthreads();
+}
+
+// M (forward) / M^* (adjoint) on every pair of the CTA, in place.  `phys`
+// maps the logical pair index (within the CTA) to its slot; `pg` the global pair.
+template <int KC, bool ADJ, bool LEFT>
+__device__ void middle_op(float2* S, int P, const float2* __restrict__ M, int box, int L, int h, int sU) {
+    const int ntask = P * KC;
+    const int nB = sU - h;
+    for (int id = threadIdx.x; id < ntask; id += blockDim.x) {
+        const int col = id / P, lp = id - col * P;
+        // threads run over physical slots (consecutive slots: no bank conflicts)
+        const int slot = lp;
+        int64_t pg;
+        if (LEFT) {   // slot -> logical sigma (inverse of the inner-end layout of the left half)
+            const int lo = L - sU;
+            const int sg = ((slot & ((1 << lo) - 1)) << nB) | rev_bits(slot >> lo, nB);
+            pg = int64_t(box) * P + sg;
+        } else {      // logical tau = slot
+            pg = int64_t(slot) * (int64_t(1) << (L - h)) + box;
+        }
+        float2* Sc = S + col * P * R;
+        float2 x[R], y[R];
+        load_pair(Sc, slot, x);
+        const float2* Mp = M + pg * R * R;
+        if (!ADJ) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                float2 row[R];
+                load_row(Mp + i * R, row);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) cfma(acc, row[jj], x[jj]);
+                y[i] = acc;
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                float2 row[R];
+                load_row(Mp + i * R, row);
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) cfmac(y[jj], row[jj], x[i]);
+            }
+        }
+        store_pair(Sc, slot, y);
+    }
+    __syncthreads();
+}
+
+struct HalfArgs {
+    const float2* X;     // outer input vectors (N x k, ld) or middle state
+    int64_t ldx;
+    float2* Y;           // outer output vectors or middle state
+    int64_t ldy;
+    float2* mid;         // middle state [col][N][R]
+    const float2* VP;
+    const float2* UP;
+    const float2* M;
+    const float* P;      // PV | PU | Pc
+    int pu_off, pc_off;
+    Tabs tab;            // left: E tables by s - h ; right: F tables by s - sV
+    int n, L, h, sU, sV, k;
+};
+
+// Left half, one CTA per space box tau_h (blockIdx.x) and KC columns (blockIdx.y).
+// ADJ: g -> U^* -> B^* levels -> M^* -> middle.   !ADJ: middle -> B levels -> U -> y.
+template <int KC, bool ADJ>
+__global__ void __launch_bounds__(256, 2) k_bf_left(HalfArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* S = reinterpret_cast<float2*>(smem4);
+    const int L = a.L, h = a.h, sU = a.sU;
+    const int P = 1 << (L - h);
+    float* sPc = reinterpret_cast<float*>(S + KC * P * R);
+    float* sPU = sPc + 2 * PCS;
+    const int lsU = 1 << (L - sU), nbU = lsU;
+    for (int e = threadIdx.x; e < 2 * R * R; e += blockDim.x) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
+    for (int e = threadIdx.x; e < lsU * R; e += blockDim.x) sPU[e] = a.P[a.pu_off + e];
+    const int box = blockIdx.y, col0 = blockIdx.x * KC;
+    const int kc = min(KC, a.k - col0);
+    __syncthreads();
+    if (ADJ) {
+        // U^*: d(leaf, b, i) = sum_q PU[q][i] conj(UP[x_q][b]) g(x_q)
+        for (int id = threadIdx.x; id < P * KC; id += blockDim.x) {
+            const int col = id / P, lp = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = lp / nbU, b = lp - leaf * nbU;
+            const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsU;
+            const float2* g = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 y[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) y[i] = make_float2(0.f, 0.f);
+            for (int qq = 0; qq < lsU; ++qq) {
+                const float2 m = cmulc(__ldg(a.UP + (x0 + qq) * nbU + b), g[qq]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float pu = sPU[qq * R + i];
+                    y[i].x = fmaf(pu, m.x, y[i].x);
+                    y[i].y = fmaf(pu, m.y, y[i].y);
+                }
+            }
+            store_pair(S + col * P * R, lp, y);
+        }
+        __syncthreads();
+        for (int s = sU - 1; s >= h; --s)
+            level_op<KC, true, false, true>(S, P, sPc, a.tab.t[s - h], box, s, L, h, sU);
+        middle_op<KC, true, true>(S, P, a.M, box, L, h, sU);
+        // middle state out (logical sigma order)
+        const int nB = sU - h;
+        for (int id = threadIdx.x; id < P * R * KC; id += blockDim.x) {
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << (L - sU)) | (lp >> nB);
+            a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i] = S[col * P * R + sw(slot, i)];
+        }
+    } else {
+        const int nB = sU - h;
+        for (int id = threadIdx.x; id < P * R * KC; id += blockDim.x) {
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << (L - sU)) | (lp >> nB);
+            S[col * P * R + sw(slot, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i];
+        }
+        __syncthreads();
+        for (int s = h; s < sU; ++s)
+            level_op<KC, true, true, false>(S, P, sPc, a.tab.t[s - h], box, s, L, h, sU);
+        // U: y(x) = sum_b UP[x][b] sum_i PU[q][i] d(leaf, b, i)
+        for (int id = threadIdx.x; id < P * KC; id += blockDim.x) {
+            const int col = id / P, xl = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = xl / lsU, qq = xl - leaf * lsU;
+            const int64_t xg = int64_t(box) * P + xl;
+            const float2* Sc = S + col * P * R;
+            float2 out = make_float2(0.f, 0.f);
+            for (int b = 0; b < nbU; ++b) {
+                float2 d[R];
+                load_pair(Sc, leaf * nbU + b, d);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float pu = sPU[qq * R + i];
+                    acc.x = fmaf(pu, d[i].x, acc.x);
+                    acc.y = fmaf(pu, d[i].y, acc.y);
+                }
+                cfma(out, __ldg(a.UP + xg * nbU + b), acc);
+            }
+            a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
+        }
+    }
+}
+
+// Right half, one CTA per frequency box sigma_h (blockIdx.x) and KC columns.
+// ADJ: middle -> C^* levels -> V^* -> f.   !ADJ: f -> V -> C levels -> M -> middle.
+template <int KC, bool ADJ>
+__global__ void __launch_bounds__(256, 2) k_bf_right(HalfArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* S = reinterpret_cast<float2*>(smem4);
+    const int L = a.L, h = a.h, sV = a.sV;
+    const int P = 1 << h;
+    float* sPc = reinterpret_cast<float*>(S + KC * P * R);
+    float* sPV = sPc + 2 * PCS;
+    const int lsV = 1 << sV, na = 1 << sV, nl = 1 << (h - sV);
+    for (int e = threadIdx.x; e < 2 * R * R; e += blockDim.x) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
+    for (int e = threadIdx.x; e < lsV * R; e += blockDim.x) sPV[e] = a.P[e];
+    const int box = blockIdx.y, col0 = blockIdx.x * KC;
+    const int kc = min(KC, a.k - col0);
+    const int64_t nmid = int64_t(1) << (L - h);
+    __syncthreads();
+    if (ADJ) {
+        for (int id = threadIdx.x; id < P * R * KC; id += blockDim.x) {
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            S[col * P * R + sw(lp, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i];
+        }
+        __syncthreads();
+        for (int s = h - 1; s >= sV; --s)
+            level_op<KC, false, true, true>(S, P, sPc, a.tab.t[s - sV], box, s, L, h, a.sU);
+        // V^*: f(xi) = sum_a conj(VP[a][xi]) sum_t PV[q][t] c(a, leaf, t)
+        for (int id = threadIdx.x; id < P * KC; id += blockDim.x) {
+            const int col = id / P, xl = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = xl >> sV, qq = xl & (lsV - 1);
+            const int64_t xg = int64_t(box) * P + xl;
+            const float2* Sc = S + col * P * R;
+            const int slotl = rev_bits(leaf, h - sV);
+            float2 out = make_float2(0.f, 0.f);
+            for (int aa = 0; aa < na; ++aa) {
+                float2 c[R];
+                load_pair(Sc, aa * nl + slotl, c);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    const float pv = sPV[qq * R + t];
+                    acc.x = fmaf(pv, c[t].x, acc.x);
+                    acc.y = fmaf(pv, c[t].y, acc.y);
+                }
+                cfmac(out, __ldg(a.VP + int64_t(aa) * a.n + xg), acc);
+            }
+            a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
+        }
+    } else {
+        // V: c(a, leaf, j) = sum_q PV[q][j] VP[a][xi_q] f(xi_q)
+        for (int id = threadIdx.x; id < P * KC; id += blockDim.x) {
+            const int col = id / P, lp = id - col * P;
+            if (col >= kc) continue;
+            const int aa = lp / nl, leaf = lp - aa * nl;
+            const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsV;
+            const float2* f = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 y[R];
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
+            for (int qq = 0; qq < lsV; ++qq) {
+                const float2 m = cmul(__ldg(a.VP + int64_t(aa) * a.n + x0 + qq), f[qq]);
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) {
+                    const float pv = sPV[qq * R + jj];
+                    y[jj].x = fmaf(pv, m.x, y[jj].x);
+                    y[jj].y = fmaf(pv, m.y, y[jj].y);
+                }
+            }
+            store_pair(S + col * P * R, aa * nl + rev_bits(leaf, h - sV), y);
+        }
+        __syncthreads();
+        for (int s = sV; s < h; ++s)
+            level_op<KC, false, false, false>(S, P, sPc, a.tab.t[s - sV], box, s, L, h, a.sU);
+        middle_op<KC, false, false>(S, P, a.M, box, L, h, a.sU);
+        for (int id = threadIdx.x; id < P * R * KC; id += blockDim.x) {
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i] = S[col * P * R + sw(lp, i)];
+        }
+    }
+}
+
+template <int KC>
+size_t half_smem(int P) {
+    return size_t(KC) * P * R * sizeof(float2) + (2 * PCS + 8 * R) * sizeof(float);
+}
+
+// first/second: the two halves in execution order (adjoint: left then right;
+// forward: right then left), each with its own table set.
+template <int KC>
+fio_status launch_fused_pass(const fio_bf* bf, const HalfArgs& first, const HalfArgs& second, bool adjoint, int kcols,
+                             cudaStream_t st) {
+    const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
+    const int nchunk = (kcols + KC - 1) / KC;
+    // column chunks of one box are consecutive in launch order: they run together and share the
+    // box's factor tables through L2
+    dim3 gl(nchunk, 1 << bf->h), gr(nchunk, 1 << (bf->L - bf->h));
+    const size_t shl = half_smem<KC>(Pl), shr = half_smem<KC>(Pr);
+    static bool attr_done = false;
+    if (!attr_done) {
+        const int mx = 110 * 1024;
+        cudaFuncSetAttribute(k_bf_left<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bf_left<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bf_right<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bf_right<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr_done = true;
+    }
+    if (adjoint) {
+        FIO_LAUNCH("k_bf_left_adj", st, k_bf_left<KC, true><<<gl, 256, shl, st>>>(first));
+        FIO_LAUNCH("k_bf_right_adj", st, k_bf_right<KC, true><<<gr, 256, shr, st>>>(second));
+    } else {
+        FIO_LAUNCH("k_bf_right_fwd", st, k_bf_right<KC, false><<<gr, 256, shr, st>>>(first));
+        FIO_LAUNCH("k_bf_left_fwd", st, k_bf_left<KC, false><<<gl, 256, shl, st>>>(second));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+}  // namespace
+
+bool bf_fused_ok(const fio_bf* bf) {
+    if (bf->r != R || bf->L < 6) return false;
+    const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
+    return Pl <= 512 && Pr <= 512 && bf->sU - bf->h <= 23 && bf->h - bf->sV <= 23;
+}
+
+// Columns per CTA: 64 KiB of in-place state (KC * P * 128 B) per CTA, two CTAs per SM.
+int bf_fused_kc(const fio_bf* bf) {
+    const int P = std::max(1 << (bf->L - bf->h), 1 << bf->h);
+    return P <= 128 ? 4 : (P <= 256 ? 2 : 1);
+}
+
+fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kcols, int adjoint,
+                          float2* mid, cudaStream_t st) {
+    HalfArgs a;
+    a.X = X;
+    a.ldx = ld;
+    a.Y = Y;
+    a.ldy = ld;
+    a.mid = mid;
+    a.VP = bf->VP.as<float2>();
+    a.UP = bf->UP.as<float2>();
+    a.M = bf->M.as<float2>();
+    a.P = bf->P.as<float>();
+    a.pu_off = int(bf->pu_off());
+    a.pc_off = int(bf->pc_off());
+    a.n = bf->n;
+    a.L = bf->L;
+    a.h = bf->h;
+    a.sU = bf->sU;
+    a.sV = bf->sV;
+    a.k = kcols;
+    // the left kernels read E tables (B levels), the right kernels F tables (C levels)
+    Tabs tl{}, tr{};
+    for (size_t i = 0; i < bf->B.size() && i < 24; ++i) tl.t[i] = bf->B[i].as<float2>();
+    for (size_t i = 0; i < bf->C.size() && i < 24; ++i) tr.t[i] = bf->C[i].as<float2>();
+    const int KC = bf_fused_kc(bf);
+    if (adjoint) {
+        a.tab = tl;
+        HalfArgs b = a;
+        b.tab = tr;
+        // left pass reads X, writes mid; right pass reads mid, writes Y
+        if (KC == 4) FIO_TRY(launch_fused_pass<4>(bf, a, b, true, kcols, st));
+        else if (KC == 2) FIO_TRY(launch_fused_pass<2>(bf, a, b, true, kcols, st));
+        else FIO_TRY(launch_fused_pass<1>(bf, a, b, true, kcols, st));
+    } else {
+        a.tab = tr;
+        HalfArgs b = a;
+        b.tab = tl;
+        if (KC == 4) FIO_TRY(launch_fused_pass<4>(bf, a, b, false, kcols, st));
+        else if (KC == 2) FIO_TRY(launch_fused_pass<2>(bf, a, b, false, kcols, st));
+        else FIO_TRY(launch_fused_pass<1>(bf, a, b, false, kcols, st));
+    }
+    return FIO_OK;
+}
+
+}  // namespace fio

@@ -310,40 +310,91 @@ template <class C> __global__ void k_to_f64(const C* __restrict__ a, double2* __
 }
 
 // ------------------------------------------------------------- solve
-// up:  z = W_t y_t;  rows < m-r -> bh1 (rows t*(m-r)), rows >= m-r -> ynext (rows t*r)
-__global__ void k_ulv_up(const float2* __restrict__ W, int64_t nodes, int m, int r, const float2* __restrict__ y,
-                         int64_t ldy, float2* __restrict__ bh1, int64_t ldb, float2* __restrict__ ynext, int64_t ldn) {
-    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= nodes * m) return;
-    int col = blockIdx.y;
-    int64_t t = e / m;
-    int i = int(e % m);
-    const float2* Wt = W + t * m * m;
-    const float2* yt = y + col * ldy + t * m;
-    float2 a = make_float2(0.f, 0.f);
-    for (int j = 0; j < m; ++j) cfma(a, Wt[i + int64_t(j) * m], yt[j]);
-    const int n1 = m - r;
-    if (i < n1) bh1[col * ldb + t * n1 + i] = a;
-    else ynext[col * ldn + t * r + (i - n1)] = a;
-}
+// Batched node products of the solve, one CTA per (node, chunk of KCOL
+// columns, block of 256 output rows):
+//   up:   z = W_t y_t                 (CONJ = false)
+//   down: c = W_t^* [bh1_t; c2_t]     (CONJ = true)
+// The m-vector of a node is split into rows [0, nA) read from inA (node
+// offset t*nA) and rows [nA, m) from inB (node offset t*(m-nA)); the result
+// into rows [0, nC) of outC (offset t*nC) and [nC, m) of outD (offset
+// t*(m-nC)).  W (column-major m x m) and x are staged through shared memory
+// in tiles of WT inner indices; each thread owns rows i0 + 32 q of its row
+// block and two columns.
+constexpr int KCOL = 16;
+constexpr int WT = 32;
+constexpr int RB = 128;   // rows per CTA: 4 per thread
 
-// down: c_t = W_t^* [bh1_t; c2_t],  c2_t = cpar rows t*r..
-__global__ void k_ulv_down(const float2* __restrict__ W, int64_t nodes, int m, int r, const float2* __restrict__ bh1,
-                           int64_t ldb, const float2* __restrict__ cpar, int64_t ldp, float2* __restrict__ out,
-                           int64_t ldo) {
-    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= nodes * m) return;
-    int col = blockIdx.y;
-    int64_t t = e / m;
-    int c = int(e % m);
-    const int n1 = m - r;
-    const float2* Wc = W + t * m * m + int64_t(c) * m;
-    const float2* b = bh1 + col * ldb + t * n1;
-    const float2* p = cpar + col * ldp + t * r;
-    float2 a = make_float2(0.f, 0.f);
-    for (int i = 0; i < n1; ++i) cfmac(a, Wc[i], b[i]);
-    for (int i = 0; i < r; ++i) cfmac(a, Wc[n1 + i], p[i]);
-    out[col * ldo + e] = a;
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
+                                                       int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
+                                                       float2* __restrict__ outC, int nC, int64_t ldC,
+                                                       float2* __restrict__ outD, int64_t ldD, int k) {
+    __shared__ float2 sx[WT * KCOL];       // sx[jj * KCOL + c]
+    __shared__ float2 sw[WT * RB];         // sw[jj * RB + il]
+    const int t = blockIdx.x, c0 = blockIdx.y * KCOL, r0 = blockIdx.z * RB, tid = threadIdx.x;
+    const int kc = min(KCOL, k - c0), nr = min(RB, m - r0);
+    const float2* Wt = W + int64_t(t) * m * m;
+    const int i0 = tid & 31, cg = tid >> 5;   // 8 column groups of 2
+    float2 acc[RB / 32][2];
+#pragma unroll
+    for (int q = 0; q < RB / 32; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < m; j0 += WT) {
+        const int jw = min(WT, m - j0);
+        __syncthreads();
+        for (int e = tid; e < WT * KCOL; e += blockDim.x) {
+            const int jj = e / KCOL, c = e % KCOL, j = j0 + jj;
+            float2 v = make_float2(0.f, 0.f);
+            if (jj < jw && c < kc)
+                v = (j < nA) ? inA[int64_t(c0 + c) * ldA + int64_t(t) * nA + j]
+                             : inB[int64_t(c0 + c) * ldB + int64_t(t) * (m - nA) + (j - nA)];
+            sx[e] = v;
+        }
+        for (int e = tid; e < jw * nr; e += blockDim.x) {
+            int jj, il;
+            float2 v;
+            if (!CONJ) {   // columns j of W, rows r0..: W[i + j m]
+                il = e % nr;
+                jj = e / nr;
+                v = Wt[(r0 + il) + int64_t(j0 + jj) * m];
+            } else {       // rows j of W, columns r0..: W[j + i m]
+                jj = e % jw;
+                il = e / jw;
+                v = Wt[(j0 + jj) + int64_t(r0 + il) * m];
+            }
+            sw[jj * RB + il] = v;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < jw; ++jj) {
+            const float2 x0 = sx[jj * KCOL + 2 * cg], x1 = sx[jj * KCOL + 2 * cg + 1];
+#pragma unroll
+            for (int q = 0; q < RB / 32; ++q) {
+                const int il = i0 + 32 * q;
+                if (il < nr) {
+                    const float2 w = sw[jj * RB + il];
+                    if (CONJ) {
+                        cfmac(acc[q][0], w, x0);
+                        cfmac(acc[q][1], w, x1);
+                    } else {
+                        cfma(acc[q][0], w, x0);
+                        cfma(acc[q][1], w, x1);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RB / 32; ++q) {
+        const int il = i0 + 32 * q;
+        if (il >= nr) continue;
+        const int i = r0 + il;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = 2 * cg + u;
+            if (c >= kc) continue;
+            if (i < nC) outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = acc[q][u];
+            else outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[q][u];
+        }
+    }
 }
 
 __global__ void k_gemv_sq(const float2* __restrict__ A, int m, const float2* __restrict__ x, int64_t ldx,
@@ -394,6 +445,10 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
     for (int l = Lh; l >= 1; --l) {
         const int nn = 1 << l;
         const bool f64 = nn <= kFp64Nodes;
+        if (h->m(l) == 0) {   // empty level: all ranks at and above it are 0
+            cur_f64 = f64;
+            continue;
+        }
         const int r = h->ranks[l];
         int cur = l & 1;
         // inputs of this level: leaf generators, or D+/U+ of the merge (in dplus/uplus)
@@ -495,13 +550,15 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
     float2* X = static_cast<float2*>(Xv);
     for (int l = Lh; l >= 1; --l) {
         const int m = h->m(l), r = h->ranks[l];
+        if (m == 0) continue;   // every rank above this level is 0: nothing to pass up
         const float2* in = (l == Lh) ? B : yv(l);
         int64_t ldin = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        dim3 g(cdiv((int64_t(1) << l) * m, TB), k);
+        dim3 gg(1 << l, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
         FIO_LAUNCH("k_ulv_up", st,
-                   k_ulv_up<<<g, TB, 0, st>>>(h->W[l].as<float2>(), int64_t(1) << l, m, r, in, ldin, bh(l),
-                                              std::max<int64_t>(nb, 1), yv(l - 1), std::max<int64_t>(h->rows(l - 1), 1)));
+                   k_ulv_node_gemm<false><<<gg, 256, 0, st>>>(h->W[l].as<float2>(), m, in, m, ldin, in, ldin, bh(l),
+                                                                m - r, std::max<int64_t>(nb, 1), yv(l - 1),
+                                                                std::max<int64_t>(h->rows(l - 1), 1), k));
     }
     const int m0 = 2 * h->ranks[1];
     if (m0 > 0) {
@@ -510,14 +567,16 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
     }
     for (int l = 1; l <= Lh; ++l) {
         const int m = h->m(l), r = h->ranks[l];
+        if (m == 0) continue;
         float2* out = (l == Lh) ? X : cv(l);
         int64_t ldo = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        dim3 g(cdiv((int64_t(1) << l) * m, TB), k);
+        dim3 gg(1 << l, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
         FIO_LAUNCH("k_ulv_down", st,
-                   k_ulv_down<<<g, TB, 0, st>>>(h->W[l].as<float2>(), int64_t(1) << l, m, r, bh(l),
-                                                std::max<int64_t>(nb, 1), cv(l - 1),
-                                                std::max<int64_t>(h->rows(l - 1), 1), out, ldo));
+                   k_ulv_node_gemm<true><<<gg, 256, 0, st>>>(h->W[l].as<float2>(), m, bh(l), m - r,
+                                                               std::max<int64_t>(nb, 1), cv(l - 1),
+                                                               std::max<int64_t>(h->rows(l - 1), 1), out, m, ldo, out,
+                                                               ldo, k));
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;

@@ -23,13 +23,14 @@ def _cuda():
     import paper_2609_11520_b300  # noqa: F401  (fails loudly if the library is missing)
 
 
+@pytest.mark.parametrize("path", ["per_level", "auto"])
 @pytest.mark.parametrize("kind,s", [("cabs", 1.0), ("dft", 1.0), ("cabs", 0.6)])
-@pytest.mark.parametrize("n", [16, 64, 256, 2048])
-@pytest.mark.parametrize("k", [1, 3])
-def test_bf_apply_matches_oracle(kind, s, n, k):
+@pytest.mark.parametrize("n", [16, 64, 128, 256, 2048, 8192])
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_bf_apply_matches_oracle(kind, s, n, k, path):
     from paper_2609_11520_b300 import BF
     ob = Butterfly1D(Phase(kind, s), n, 16)
-    gb = BF(n, 16, kind, s)
+    gb = BF(n, 16, kind, s).set_path(path)
     f = crandn(n, k, seed=n + k)
     y_ref = ob.apply(f)
     y = to_np(gb.apply(to_dev(f)))
@@ -51,12 +52,13 @@ def test_bf_apply_other_ranks(r):
     assert rel(to_np(gb.adjoint(to_dev(f))), ob.adjoint(f)) < TOL
 
 
-def test_bf_apply_column_blocks_with_leading_dimension():
+@pytest.mark.parametrize("path", ["per_level", "fused"])
+def test_bf_apply_column_blocks_with_leading_dimension(path):
     """k ragged (67 columns crosses the 64-column chunk), rows padded to ld > N."""
     from paper_2609_11520_b300 import BF
     n, k, ld = 512, 67, 600
     ob = Butterfly1D(Phase("cabs"), n, 16)
-    gb = BF(n, 16)
+    gb = BF(n, 16).set_path(path)
     f = crandn(n, k, seed=3)
     X = torch.zeros(k, ld, dtype=torch.complex64, device="cuda")
     X[:, :n] = to_dev(f)
@@ -73,11 +75,12 @@ def test_bf_apply_empty_block():
     assert gb.apply(X).shape == (0, 256)
 
 
-def test_bf_apply_16384_elementwise():
+@pytest.mark.parametrize("path", ["per_level", "fused"])
+def test_bf_apply_16384_elementwise(path):
     from paper_2609_11520_b300 import BF
     n = 1 << 14
     ob = Butterfly1D(Phase("cabs"), n, 16)
-    gb = BF(n, 16)
+    gb = BF(n, 16).set_path(path)
     f = crandn(n, 1, seed=11)
     assert rel(to_np(gb.apply(to_dev(f))), ob.apply(f)) < TOL
     assert rel(to_np(gb.adjoint(to_dev(f))), ob.adjoint(f)) < TOL
@@ -104,6 +107,24 @@ def test_bf_apply_full_size_sampled_rows_and_dft():
     assert rel(yd, ref_d) < TOL
     xd = to_np(gd.adjoint(to_dev(f)))
     assert rel(xd, np.fft.fftshift(np.fft.fft(f, axis=0), axes=0)) < TOL
+
+
+@pytest.mark.parametrize("n", [1 << 12, 1 << 13, 1 << 15, 1 << 16, 1 << 17, 1 << 18])
+def test_fused_equals_per_level(n):
+    """The two kernel paths agree to FP32 rounding at every size of the batched/serving workloads."""
+    from paper_2609_11520_b300 import BF
+    gb = BF(n, 16)
+    X = to_dev(crandn(n, 5, seed=n % 977))
+    for adj in (False, True):
+        a = to_np(gb.set_path("fused").apply(X, adjoint=adj))
+        b = to_np(gb.set_path("per_level").apply(X, adjoint=adj))
+        assert rel(a, b) < 2e-6
+
+
+def test_bf_set_path_rejects_unsupported():
+    from paper_2609_11520_b300 import BF, FioError
+    with pytest.raises(FioError):
+        BF(1024, 9).set_path("fused")
 
 
 def test_bf_info_levels():
