@@ -96,6 +96,21 @@ fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, f
  *   Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA. */
 fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream);
 
+/* bf_apply_noalloc -- the same products as bf_apply for callers that must
+ *   not allocate device memory (no counterpart in the paper: it serves
+ *   callers whose host framework owns all device memory, or that cannot
+ *   afford a cudaMalloc, which may synchronize the device).  The coefficient
+ *   state lives in a fixed 32 MiB array compiled into the library (held on
+ *   every GPU that loads it until exit) instead of the handle's scratch, so
+ *   this call allocates and frees nothing.  Columns are processed in chunks
+ *   that fit the array; FIO_EINVAL if one column's state (N r complex64, twice
+ *   that on the per-level path) exceeds 2^22 elements.  The first call on a
+ *   device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current: make it before any stream capture.  All calls share
+ *   the array: calls whose GPU work overlaps race, so order them on one
+ *   stream.  Arguments and errors as bf_apply. */
+fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream);
+
 /* bf_set_path -- choose the kernels of bf_apply (no paper counterpart; the
  *   results agree to FP32 rounding):  0 = automatic (fused two-pass kernels
  *   where r = 16 and n >= 64, else per-level kernels), 1 = one kernel per
