@@ -114,7 +114,9 @@ fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld
 /* bf_set_path -- choose the kernels of bf_apply (no paper counterpart; the
  *   results agree to FP32 rounding):  0 = automatic (fused two-pass kernels
  *   where r = 16 and n >= 64, else per-level kernels), 1 = one kernel per
- *   factor (per-level), 2 = fused two-pass (FIO_EINVAL where unsupported). */
+ *   factor (per-level), 2 = fused two-pass (tables staged through shared
+ *   memory where each half has 64..256 pairs per CTA), 3 = fused two-pass
+ *   without the staging.  FIO_EINVAL where a fused path is unsupported. */
 fio_status bf_set_path(fio_bf* bf, int path);
 
 /* bf_info -- sizes of a handle: out[0..7] = n, d, r, L, h, sU (space level of

@@ -48,8 +48,8 @@ class BF:
         return self._h
 
     def set_path(self, path):
-        """0 automatic, 1 per-level kernels, 2 fused two-pass kernels."""
-        check(lib.bf_set_path(self._h, int({"auto": 0, "per_level": 1, "fused": 2}.get(path, path))))
+        """0 automatic, 1 per-level kernels, 2 fused two-pass kernels, 3 fused without table staging."""
+        check(lib.bf_set_path(self._h, int({"auto": 0, "per_level": 1, "fused": 2, "fused_v2": 3}.get(path, path))))
         return self
 
     def info(self):

@@ -475,9 +475,10 @@ extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, i
 }
 
 extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
-    if (!bf || path < 0 || path > 2) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
-    if (path == 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
+    if (!bf || path < 0 || path > 3) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
+    if (path >= 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
     bf->force_unfused = (path == 1);
+    bf->fused_v2 = (path == 3);
     return FIO_OK;
 }
 

@@ -35,6 +35,7 @@ struct fio_bf {
     fio::DevBuf ws;                // two coefficient states
     int64_t table_bytes = 0;
     bool force_unfused = false;    // use the per-level kernels even where the fused pass applies
+    bool fused_v2 = false;         // fused pass without shared-memory table staging
     int64_t N() const { return int64_t(n); }
     size_t pv_off() const { return 0; }
     size_t pu_off() const { return size_t(lsV) * r; }

@@ -443,6 +443,474 @@ fio_status launch_fused_pass(const fio_bf* bf, const HalfArgs& first, const Half
     return FIO_OK;
 }
 
+
+// ===================================================================== v3
+// Same halves with 512 threads per CTA and the factor tables staged through
+// shared memory: each transfer level's phase slice (P/2 quads x 4 rows of 16
+// complex) and the middle-level blocks M (P/8 pairs per chunk) are copied with
+// cp.async into one of two buffers while the previous item is computed.  Phase
+// rows are stored by physical quad (row = qi*4 + o*2 + e, o the lane-varying
+// output half, e the summed input half) with 16-byte chunk m at m ^ ((row>>1)&7),
+// so the 8 lanes of a quarter warp (4 quads x 2 o) hit distinct banks.
+// Used where P <= 256 (then KC * P = 512: one quad task per thread and level).
+namespace v3 {
+
+constexpr int NT = 512;
+
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+    const unsigned d = unsigned(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct Geo {
+    int L, h, sU, sV, n, P;
+};
+
+// Stage the phase slice of level s (contiguous in global memory) into `buf`.
+template <bool LEFT, bool ADJ>
+__device__ void stage_level(float4* buf, const float2* __restrict__ T, int box, int s, const Geo& g) {
+    const int64_t q0 = LEFT ? (int64_t(box) << (g.L - g.h - 1)) : (int64_t(box) << (g.h - 1));
+    const float4* src = reinterpret_cast<const float4*>(T + q0 * 4 * R);
+    const int W = LEFT ? g.L - s : g.h - s;
+    const int j = LEFT ? g.sU - s : g.h - s;
+    const int half = 1 << (W - 1);
+    const int nch = (g.P / 2) * 4 * 8;
+    for (int e = threadIdx.x; e < nch; e += NT) {
+        const int m = e & 7, row = e >> 3;
+        const int ql = row >> 2, c = (row >> 1) & 1, be = row & 1;
+        const int a = ql >> (W - 1), lo = ql & (half - 1);
+        int rr;
+        if (LEFT) {
+            const int wj = W - j;
+            rr = (rev_bits(lo & ((1 << (j - 1)) - 1), j - 1) << wj) | (lo >> (j - 1));
+        } else {
+            rr = rev_bits(lo, W - 1);
+        }
+        const int qi = (a << (W - 1)) | rr;
+        const int o = ADJ ? be : c, ee = ADJ ? c : be;
+        const int drow = qi * 4 + o * 2 + ee;
+        cp16(buf + drow * 8 + (m ^ ((drow >> 1) & 7)), src + e);
+    }
+}
+
+// Stage chunk `ck` of the middle-level blocks: P/8 pairs, 256 complex each.
+// LEFT (adjoint M^*, lanes read columns): natural layout; RIGHT (forward M,
+// lanes read rows): chunk m of row (pair, i) at m ^ (i & 7).
+template <bool LEFT>
+__device__ void stage_m(float4* buf, const float2* __restrict__ M, int box, int ck, const Geo& g) {
+    const int CH = g.P / 8;
+    const int nch = CH * R * 8;
+    for (int e = threadIdx.x; e < nch; e += NT) {
+        const int m = e & 7, i = (e >> 3) & (R - 1), pl = e >> 7;
+        const int lp = ck * CH + pl;
+        const int64_t pg = LEFT ? int64_t(box) * g.P + lp : int64_t(lp) * (int64_t(1) << (g.L - g.h)) + box;
+        const float4* src = reinterpret_cast<const float4*>(M + pg * R * R) + i * 8 + m;
+        const int pos = LEFT ? m : (m ^ (i & 7));
+        cp16(buf + (pl * R + i) * 8 + pos, src);
+    }
+}
+
+template <int KC, bool LEFT, bool MS, bool ADJ>
+__device__ void level3(float2* S, const float* sPc, const float4* ph, int s, const Geo& g) {
+    const int P = g.P;
+    const int W = LEFT ? g.L - s : g.h - s;
+    const int half = 1 << (W - 1);
+    const int id = threadIdx.x;   // KC * P == NT
+    const int col = id / P, rem = id - col * P, qi = rem >> 1, o = rem & 1;
+    const int base = ((qi >> (W - 1)) << W) | (qi & (half - 1));
+    float2* Sc = S + col * P * R;
+    float2 x0[R], x1[R];
+    load_pair(Sc, base, x0);
+    load_pair(Sc, base + half, x1);
+    __syncwarp();
+    const int sw8 = (qi * 2 + o) & 7;
+    const float4* r0 = ph + (qi * 4 + o * 2 + 0) * 8;
+    const float4* r1 = ph + (qi * 4 + o * 2 + 1) * 8;
+    float2 y[R];
+    if (MS) {
+        const float* Po = sPc + o * PCS;
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+            const float4 p0 = r0[m ^ sw8], p1 = r1[m ^ sw8];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = 2 * m + u;
+                float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t4 = 0; t4 < R / 4; ++t4) {
+                    const float4 pv = *reinterpret_cast<const float4*>(Po + i * R + 4 * t4);
+                    const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int t = 4 * t4 + v;
+                        h0.x = fmaf(pp[v], x0[t].x, h0.x);
+                        h0.y = fmaf(pp[v], x0[t].y, h0.y);
+                        h1.x = fmaf(pp[v], x1[t].x, h1.x);
+                        h1.y = fmaf(pp[v], x1[t].y, h1.y);
+                    }
+                }
+                const float2 f0 = u ? make_float2(p0.z, p0.w) : make_float2(p0.x, p0.y);
+                const float2 f1 = u ? make_float2(p1.z, p1.w) : make_float2(p1.x, p1.y);
+                float2 acc = make_float2(0.f, 0.f);
+                if (!ADJ) {
+                    cfma(acc, f0, h0);
+                    cfma(acc, f1, h1);
+                } else {
+                    cfmac(acc, f0, h0);
+                    cfmac(acc, f1, h1);
+                }
+                y[i] = acc;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float4* re = e ? r1 : r0;
+            const float* Pe = sPc + e * PCS;
+#pragma unroll
+            for (int m = 0; m < R / 2; ++m) {
+                const float4 pq = re[m ^ sw8];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int t = 2 * m + u;
+                    const float2 f = u ? make_float2(pq.z, pq.w) : make_float2(pq.x, pq.y);
+                    const float2 xv = e ? x1[t] : x0[t];
+                    const float2 gg = ADJ ? cmulc(f, xv) : cmul(f, xv);
+#pragma unroll
+                    for (int j4 = 0; j4 < R / 4; ++j4) {
+                        const float4 pv = *reinterpret_cast<const float4*>(Pe + t * R + 4 * j4);
+                        y[4 * j4 + 0].x = fmaf(pv.x, gg.x, y[4 * j4 + 0].x);
+                        y[4 * j4 + 0].y = fmaf(pv.x, gg.y, y[4 * j4 + 0].y);
+                        y[4 * j4 + 1].x = fmaf(pv.y, gg.x, y[4 * j4 + 1].x);
+                        y[4 * j4 + 1].y = fmaf(pv.y, gg.y, y[4 * j4 + 1].y);
+                        y[4 * j4 + 2].x = fmaf(pv.z, gg.x, y[4 * j4 + 2].x);
+                        y[4 * j4 + 2].y = fmaf(pv.z, gg.y, y[4 * j4 + 2].y);
+                        y[4 * j4 + 3].x = fmaf(pv.w, gg.x, y[4 * j4 + 3].x);
+                        y[4 * j4 + 3].y = fmaf(pv.w, gg.y, y[4 * j4 + 3].y);
+                    }
+                }
+            }
+        }
+    }
+    store_pair(Sc, o ? base + half : base, y);
+}
+
+// One chunk of M (forward, RIGHT) or M^* (adjoint, LEFT), in place: task =
+// (pair of the chunk, column, output index), 16 lanes per (pair, column).
+template <int KC, bool LEFT>
+__device__ void mchunk3(float2* S, const float4* mb, int ck, const Geo& g) {
+    const int P = g.P, CH = P / 8;
+    const int nB = g.sU - g.h, lo = g.L - g.sU;
+    const int ntask = CH * KC * R;
+    for (int b0 = 0; b0 < ntask; b0 += NT) {
+        const int id = b0 + threadIdx.x;
+        const bool act = id < ntask;
+        const int jj = id & (R - 1), rest = id >> 4;
+        const int pl = rest % CH, col = rest / CH;
+        const int lp = ck * CH + pl;
+        const int slot = LEFT ? ((rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB)) : lp;
+        float2* Sc = S + col * P * R;
+        float2 x[R];
+        if (act) load_pair(Sc, slot, x);
+        __syncwarp();
+        if (act) {
+            const float2* mp = reinterpret_cast<const float2*>(mb + pl * R * 8);
+            float2 acc = make_float2(0.f, 0.f);
+            if (LEFT) {   // y_j = sum_i conj(M[i][j]) x_i, natural layout
+#pragma unroll
+                for (int i = 0; i < R; ++i) cfmac(acc, mp[i * R + jj], x[i]);
+            } else {      // y_i = sum_j M[i][j] x_j, row i swizzled by (i & 7)
+                const float4* rowp = mb + (pl * R + jj) * 8;
+#pragma unroll
+                for (int m = 0; m < R / 2; ++m) {
+                    const float4 v = rowp[m ^ (jj & 7)];
+                    cfma(acc, make_float2(v.x, v.y), x[2 * m]);
+                    cfma(acc, make_float2(v.z, v.w), x[2 * m + 1]);
+                }
+            }
+            Sc[sw(slot, jj)] = acc;
+        }
+    }
+}
+
+template <int KC, bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
+    extern __shared__ float4 smem4[];
+    Geo g{a.L, a.h, a.sU, a.sV, a.n, 1 << (a.L - a.h)};
+    const int P = g.P;
+    float2* S = reinterpret_cast<float2*>(smem4);
+    float4* buf0 = smem4 + KC * P * R / 2;
+    float4* buf1 = buf0 + P * 16;
+    float* sPc = reinterpret_cast<float*>(buf1 + P * 16);
+    float* sPU = sPc + 2 * PCS;
+    const int lsU = 1 << (g.L - g.sU), nbU = lsU;
+    const int box = blockIdx.y, col0 = blockIdx.x * KC;
+    const int kc = min(KC, a.k - col0);
+    const int nlev = g.sU - g.h;
+    // item sequence: transfer levels (adjoint: sU-1 .. h; forward: h .. sU-1), then
+    // (adjoint only) the 8 chunks of M^*
+    const int nitem = nlev + (ADJ ? 8 : 0);
+    auto stage = [&](int it, float4* b) {
+        if (it < nlev) {
+            const int s = ADJ ? g.sU - 1 - it : g.h + it;
+            stage_level<true, ADJ>(b, a.tab.t[s - g.h], box, s, g);
+        } else {
+            stage_m<true>(b, a.M, box, it - nlev, g);
+        }
+    };
+    if (nitem > 0) {
+        stage(0, buf0);
+        cp_commit();
+    }
+    for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
+    for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[e] = a.P[a.pu_off + e];
+    __syncthreads();
+    const int nB = nlev, lo = g.L - g.sU;
+    if (ADJ) {
+        for (int id = threadIdx.x; id < P * KC; id += NT) {   // U^*
+            const int col = id / P, lp = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = lp / nbU, b = lp - leaf * nbU;
+            const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsU;
+            const float2* gv = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 y[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) y[i] = make_float2(0.f, 0.f);
+            for (int qq = 0; qq < lsU; ++qq) {
+                const float2 mm = cmulc(__ldg(a.UP + (x0 + qq) * nbU + b), gv[qq]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float pu = sPU[qq * R + i];
+                    y[i].x = fmaf(pu, mm.x, y[i].x);
+                    y[i].y = fmaf(pu, mm.y, y[i].y);
+                }
+            }
+            store_pair(S + col * P * R, lp, y);
+        }
+    } else {
+        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB);
+            S[col * P * R + sw(slot, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i];
+        }
+    }
+    for (int it = 0; it < nitem; ++it) {
+        float4* cur = (it & 1) ? buf1 : buf0;
+        if (it + 1 < nitem) {
+            stage(it + 1, (it & 1) ? buf0 : buf1);
+            cp_commit();
+            cp_wait1();
+        } else {
+            cp_wait0();
+        }
+        __syncthreads();
+        if (it < nlev) {
+            const int s = ADJ ? g.sU - 1 - it : g.h + it;
+            if (ADJ) level3<KC, true, false, true>(S, sPc, cur, s, g);
+            else level3<KC, true, true, false>(S, sPc, cur, s, g);
+        } else {
+            mchunk3<KC, true>(S, cur, it - nlev, g);
+        }
+        __syncthreads();
+    }
+    if (ADJ) {
+        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB);
+            a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i] = S[col * P * R + sw(slot, i)];
+        }
+    } else {
+        for (int id = threadIdx.x; id < P * KC; id += NT) {   // U
+            const int col = id / P, xl = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = xl / lsU, qq = xl - leaf * lsU;
+            const int64_t xg = int64_t(box) * P + xl;
+            const float2* Sc = S + col * P * R;
+            float2 out = make_float2(0.f, 0.f);
+            for (int b = 0; b < nbU; ++b) {
+                float2 d[R];
+                load_pair(Sc, leaf * nbU + b, d);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float pu = sPU[qq * R + i];
+                    acc.x = fmaf(pu, d[i].x, acc.x);
+                    acc.y = fmaf(pu, d[i].y, acc.y);
+                }
+                cfma(out, __ldg(a.UP + xg * nbU + b), acc);
+            }
+            a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
+        }
+    }
+}
+
+template <int KC, bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
+    extern __shared__ float4 smem4[];
+    Geo g{a.L, a.h, a.sU, a.sV, a.n, 1 << a.h};
+    const int P = g.P;
+    float2* S = reinterpret_cast<float2*>(smem4);
+    float4* buf0 = smem4 + KC * P * R / 2;
+    float4* buf1 = buf0 + P * 16;
+    float* sPc = reinterpret_cast<float*>(buf1 + P * 16);
+    float* sPV = sPc + 2 * PCS;
+    const int lsV = 1 << g.sV, na = 1 << g.sV, nl = 1 << (g.h - g.sV);
+    const int box = blockIdx.y, col0 = blockIdx.x * KC;
+    const int kc = min(KC, a.k - col0);
+    const int64_t nmid = int64_t(1) << (g.L - g.h);
+    const int nlev = g.h - g.sV;
+    // adjoint: C^* levels h-1 .. sV;  forward: C levels sV .. h-1, then 8 chunks of M
+    const int nitem = nlev + (ADJ ? 0 : 8);
+    auto stage = [&](int it, float4* b) {
+        if (it < nlev) {
+            const int s = ADJ ? g.h - 1 - it : g.sV + it;
+            stage_level<false, ADJ>(b, a.tab.t[s - g.sV], box, s, g);
+        } else {
+            stage_m<false>(b, a.M, box, it - nlev, g);
+        }
+    };
+    if (nitem > 0) {
+        stage(0, buf0);
+        cp_commit();
+    }
+    for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
+    for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[e] = a.P[e];
+    __syncthreads();
+    if (ADJ) {
+        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            S[col * P * R + sw(lp, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i];
+        }
+    } else {
+        for (int id = threadIdx.x; id < P * KC; id += NT) {   // V
+            const int col = id / P, lp = id - col * P;
+            if (col >= kc) continue;
+            const int aa = lp / nl, leaf = lp - aa * nl;
+            const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsV;
+            const float2* f = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 y[R];
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
+            for (int qq = 0; qq < lsV; ++qq) {
+                const float2 mm = cmul(__ldg(a.VP + int64_t(aa) * a.n + x0 + qq), f[qq]);
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) {
+                    const float pv = sPV[qq * R + jj];
+                    y[jj].x = fmaf(pv, mm.x, y[jj].x);
+                    y[jj].y = fmaf(pv, mm.y, y[jj].y);
+                }
+            }
+            store_pair(S + col * P * R, aa * nl + rev_bits(leaf, g.h - g.sV), y);
+        }
+    }
+    for (int it = 0; it < nitem; ++it) {
+        float4* cur = (it & 1) ? buf1 : buf0;
+        if (it + 1 < nitem) {
+            stage(it + 1, (it & 1) ? buf0 : buf1);
+            cp_commit();
+            cp_wait1();
+        } else {
+            cp_wait0();
+        }
+        __syncthreads();
+        if (it < nlev) {
+            const int s = ADJ ? g.h - 1 - it : g.sV + it;
+            if (ADJ) level3<KC, false, true, true>(S, sPc, cur, s, g);
+            else level3<KC, false, false, false>(S, sPc, cur, s, g);
+        } else {
+            mchunk3<KC, false>(S, cur, it - nlev, g);
+        }
+        __syncthreads();
+    }
+    if (ADJ) {
+        for (int id = threadIdx.x; id < P * KC; id += NT) {   // V^*
+            const int col = id / P, xl = id - col * P;
+            if (col >= kc) continue;
+            const int leaf = xl >> g.sV, qq = xl & (lsV - 1);
+            const int64_t xg = int64_t(box) * P + xl;
+            const float2* Sc = S + col * P * R;
+            const int slotl = rev_bits(leaf, g.h - g.sV);
+            float2 out = make_float2(0.f, 0.f);
+            for (int aa = 0; aa < na; ++aa) {
+                float2 c[R];
+                load_pair(Sc, aa * nl + slotl, c);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    const float pv = sPV[qq * R + t];
+                    acc.x = fmaf(pv, c[t].x, acc.x);
+                    acc.y = fmaf(pv, c[t].y, acc.y);
+                }
+                cfmac(out, __ldg(a.VP + int64_t(aa) * a.n + xg), acc);
+            }
+            a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
+        }
+    } else {
+        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
+            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
+            if (col >= kc) continue;
+            a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i] = S[col * P * R + sw(lp, i)];
+        }
+    }
+}
+
+inline size_t smem3(int KC, int P) {
+    return size_t(KC) * P * R * 8 + size_t(2) * P * 256 + (2 * PCS + 8 * R) * sizeof(float);
+}
+
+template <int KC, bool ADJ>
+fio_status launch_left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
+    const int P = 1 << (bf->L - bf->h);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_left3<KC, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
+    FIO_LAUNCH(ADJ ? "k_bf_left_adj" : "k_bf_left_fwd", st, k_left3<KC, ADJ><<<g, NT, smem3(KC, P), st>>>(a));
+    return FIO_OK;
+}
+
+template <int KC, bool ADJ>
+fio_status launch_right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
+    const int P = 1 << bf->h;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_right3<KC, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
+    FIO_LAUNCH(ADJ ? "k_bf_right_adj" : "k_bf_right_fwd", st, k_right3<KC, ADJ><<<g, NT, smem3(KC, P), st>>>(a));
+    return FIO_OK;
+}
+
+template <bool ADJ>
+fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
+    switch (1 << (bf->L - bf->h)) {
+        case 64: return launch_left3<8, ADJ>(bf, a, kcols, st);
+        case 128: return launch_left3<4, ADJ>(bf, a, kcols, st);
+        default: return launch_left3<2, ADJ>(bf, a, kcols, st);
+    }
+}
+template <bool ADJ>
+fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
+    switch (1 << bf->h) {
+        case 64: return launch_right3<8, ADJ>(bf, a, kcols, st);
+        case 128: return launch_right3<4, ADJ>(bf, a, kcols, st);
+        default: return launch_right3<2, ADJ>(bf, a, kcols, st);
+    }
+}
+
+}  // namespace v3
+
 }  // namespace
 
 bool bf_fused_ok(const fio_bf* bf) {
@@ -481,6 +949,21 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
     Tabs tl{}, tr{};
     for (size_t i = 0; i < bf->B.size() && i < 24; ++i) tl.t[i] = bf->B[i].as<float2>();
     for (size_t i = 0; i < bf->C.size() && i < 24; ++i) tr.t[i] = bf->C[i].as<float2>();
+    const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
+    if (Pl >= 64 && Pl <= 256 && Pr >= 64 && Pr <= 256 && !bf->fused_v2) {
+        HalfArgs al = a, ar = a;
+        al.tab = tl;
+        ar.tab = tr;
+        if (adjoint) {
+            FIO_TRY(v3::left3<true>(bf, al, kcols, st));
+            FIO_TRY(v3::right3<true>(bf, ar, kcols, st));
+        } else {
+            FIO_TRY(v3::right3<false>(bf, ar, kcols, st));
+            FIO_TRY(v3::left3<false>(bf, al, kcols, st));
+        }
+        FIO_CUDA(cudaGetLastError());
+        return FIO_OK;
+    }
     const int KC = bf_fused_kc(bf);
     if (adjoint) {
         a.tab = tl;

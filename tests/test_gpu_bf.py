@@ -75,7 +75,7 @@ def test_bf_apply_empty_block():
     assert gb.apply(X).shape == (0, 256)
 
 
-@pytest.mark.parametrize("path", ["per_level", "fused"])
+@pytest.mark.parametrize("path", ["per_level", "fused", "fused_v2"])
 def test_bf_apply_16384_elementwise(path):
     from paper_2609_11520_b300 import BF
     n = 1 << 14
@@ -109,7 +109,7 @@ def test_bf_apply_full_size_sampled_rows_and_dft():
     assert rel(xd, np.fft.fftshift(np.fft.fft(f, axis=0), axes=0)) < TOL
 
 
-@pytest.mark.parametrize("n", [1 << 12, 1 << 13, 1 << 15, 1 << 16, 1 << 17, 1 << 18])
+@pytest.mark.parametrize("n", [1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18])
 def test_fused_equals_per_level(n):
     """The two kernel paths agree to FP32 rounding at every size of the batched/serving workloads."""
     from paper_2609_11520_b300 import BF
@@ -118,7 +118,9 @@ def test_fused_equals_per_level(n):
     for adj in (False, True):
         a = to_np(gb.set_path("fused").apply(X, adjoint=adj))
         b = to_np(gb.set_path("per_level").apply(X, adjoint=adj))
+        c = to_np(gb.set_path("fused_v2").apply(X, adjoint=adj))
         assert rel(a, b) < 2e-6
+        assert rel(c, b) < 2e-6
 
 
 def test_bf_set_path_rejects_unsupported():
