@@ -145,12 +145,54 @@ def kernel_bytes(name, N, r, kc, binfo, hinfo):
     return None
 
 
+def kernel_fma(name, N, r, kc, binfo):
+    """FP32 FMA instructions (per thread-lane) of one launch of a fused half pass, as the kernels issue them.
+
+    Transfer level: per quad and column 2 x 1152 FMA (16 x 16 real Lagrange matrix applied to the
+    real and imaginary parts of both halves, plus the complex phase products); middle level:
+    r^2 complex MACs (4 FMA) per pair; leaf levels: 8 x (16 x 2 + 4) FMA per pair or point.
+    """
+    nB, nC = binfo["sU"] - binfo["h"], binfo["h"] - binfo["sV"]
+    quad = (N // 2) * 2 * 1152
+    leaf = N * 8 * (2 * r + 4)
+    mid = N * r * r * 4
+    if name.startswith("k_bf_left"):
+        return kc * (nB * quad + leaf + (mid if name.endswith("adj") else 0))
+    if name.startswith("k_bf_right"):
+        return kc * (nC * quad + leaf + (mid if name.endswith("fwd") else 0))
+    return None
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak of a B300: 148 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def parse_profile(text):
     out = {}
     for line in text.strip().splitlines():
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+def roofline_entry(name, per_launch_ms, nbytes, nfma, hbm_peak, peak_src, clocks):
+    """Roofline of the dominant kernel.  Fused BF half passes are FP32-ALU bound at wide k (their DRAM
+    bytes equal the algorithmic bytes, profiles/k_bf_fused_*), so they report FP32 FLOP/s against
+    the FP32 FMA peak at the maximum SM clock; other kernels report HBM bytes."""
+    hbm_achieved = nbytes / (per_launch_ms / 1e3) / 1e9 if nbytes else None
+    if nfma:
+        sm_max = clocks.get("sm_max_mhz") or 2032.0
+        peak = fp32_peak_tflops(sm_max)
+        achieved = 2 * nfma / (per_launch_ms / 1e3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 x %.0f MHz" % sm_max,
+                "flops_per_launch": 2 * nfma, "bytes_per_launch": nbytes,
+                "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,
+                "traffic": None}
+    return {"kernel": name, "bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src,
+            "bytes_per_launch": nbytes, "traffic": None}
 
 
 def cpu_oracle_online(n, steps, warmup, leaf, r, rank_per_level=8, seed=3):
@@ -200,6 +242,94 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """Batched workload: 32 operators, N uniform over 2^12..2^17, 16 RHS each, one step = all 512 RHS."""
+    import torch
+    from fio_inputs import batched_operators
+    from paper_2609_11520_b300 import BF, HSS, Batch
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    ops = []
+    for i, (n, sdepth) in enumerate(batched_operators()):
+        bf = BF(n, 16, "cabs", sdepth)
+        ops.append((bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=40 + i).factor()))
+    t_build = time.perf_counter() - t0
+    k = 16
+    Us = [torch.from_numpy(np.ascontiguousarray(crandn(bf.n, k, 60 + i).T.astype(np.complex64))).cuda()
+          for i, (bf, _) in enumerate(ops)]
+    Fs = [torch.empty_like(U) for U in Us]
+    b = Batch(ops)
+    report = b.autotune(Us, Fs, reps=3)
+    times = {}
+    for mode in ("per_operator", "grouped", "graph"):
+        b.set_mode(mode)
+        for _ in range(args.warmup):
+            b.solve(Us, Fs)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(args.steps):
+            b.solve(Us, Fs)
+        ev[1].record()
+        ev[1].synchronize()
+        times[mode] = ev[0].elapsed_time(ev[1]) / args.steps
+    best = min(times, key=times.get)
+    nrhs = k * len(ops)
+    line = {"metric": "RHS solves/s, batched workload (32 uneven 1D operators x 16 RHS)", "value": nrhs / (times[best] / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": times[best],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batched1d: 32 operators, N uniform over {2^12..2^17} (seed 4), s ~ U[0.5, 1], "
+                                   "BF r 16, HSS leaf 128 tol 1e-3, 16 RHS each", "offline_build_s": round(t_build, 2),
+                       "ms_per_step_by_mode": times, "mode": best, "autotune": report.strip().splitlines()}}
+    print(json.dumps(line))
+
+
+def run_serving(args):
+    """Serving workload: resident operators, Poisson arrivals, 1..32 RHS per request, p50 / p99."""
+    import torch
+    from fio_inputs import poisson_requests
+    from paper_2609_11520_b300 import BF, HSS
+    from paper_2609_11520_b300.serve import Server, latency_stats
+    torch.cuda.set_device(0)
+    specs = [(1 << 14, 1.0), (1 << 15, 1.0), (1 << 16, 1.0), (1 << 16, 0.5), (1 << 17, 1.0), (1 << 18, 1.0)]
+    ops = {}
+    for i, (n, sdepth) in enumerate(specs):
+        bf = BF(n, 16, "cabs", sdepth)
+        ops[f"n{n}_s{sdepth}"] = (bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=70 + i).factor())
+    names = sorted(ops)
+    nreq = args.requests
+
+    def trace(rate, seed):
+        t, oi, ks = poisson_requests(nreq, rate, len(names), seed=seed, kmax=32)
+        rng = np.random.default_rng(seed)
+        out = []
+        for ti, o, kk in zip(t, oi, ks):
+            n = ops[names[o]][0].n
+            u = (rng.standard_normal((kk, n)) + 1j * rng.standard_normal((kk, n))).astype(np.complex64)
+            out.append((float(ti), names[o], torch.from_numpy(u).pin_memory()))
+        return out
+
+    # saturated throughput: every request arrives at t = 0
+    sat_trace = [(0.0, o, u) for _, o, u in trace(1.0, 5)]
+    Server(ops, kmax=64, n_slots=4).run(sat_trace[: min(200, nreq)])   # warm-up
+    sat = latency_stats(Server(ops, kmax=64, n_slots=4).run(sat_trace))
+    avg_k = np.mean([u.shape[0] for _, _, u in sat_trace])
+    req_rate = sat["rhs_per_s"] / avg_k
+    rates = {}
+    for frac in (0.5, 0.8, 1.0):
+        st = latency_stats(Server(ops, kmax=64, n_slots=4).run(trace(frac * req_rate, 5)))
+        rates[str(frac)] = {k_: round(v, 4) if isinstance(v, float) else v for k_, v in st.items()}
+    line = {"metric": "RHS solves/s served (continuous batching, Poisson arrivals); p50/p99 latency",
+            "value": sat["rhs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": nreq, "warmup": min(200, nreq),
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic",
+            "config": {"workload": "serving: 6 resident 1D operators (N = 2^14, 2^15, 2^16, 2^16 with s = 0.5, 2^17, "
+                                   "2^18), Poisson arrivals (seed 5), 1..32 RHS per request, kmax 64, 4 streams, "
+                                   "host-resident requests (H2D and D2H inside the latency)",
+                       "requests": nreq, "saturated": sat, "by_rate_fraction": rates}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,10 +337,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--workload", default="large1d", choices=["large1d", "batched1d", "serving"])
+    ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched1d":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist
@@ -319,6 +455,7 @@ def main():
     per_launch_ms = top[1][1] / top[1][0]
     nbytes = kernel_bytes(top[0], n, r, kc, binfo, hinfo)
     achieved = nbytes / (per_launch_ms / 1e3) / 1e9 if nbytes else None
+    nfma = kernel_fma(top[0], n, r, kc, binfo)
     kernels = {name: {"launches": c, "ms_total": round(ms, 4), "share": round(ms / sum(v[1] for v in prof.values()), 4)}
                for name, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
@@ -347,9 +484,7 @@ def main():
                     "d2h_bytes_per_step": int(U.numel() * 8)},
             "gpu_launches": int(launches),
             "kernels": kernels,
-            "roofline": {"kernel": top[0], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
-                         "bytes_per_launch": nbytes, "traffic": None},
+            "roofline": roofline_entry(top[0], per_launch_ms, nbytes, nfma, peak, peak_src, clk.summary()),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }

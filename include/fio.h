@@ -183,6 +183,37 @@ fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int
 
 void hss_free(fio_hss* hss);
 
+/* ------------------------------------------------------------------------
+ * Batched online stage over several resident operators of uneven size (the
+ * batched workload: many independent 1D operators, a block of RHS each; no
+ * paper counterpart beyond applying Eq. 4.2 to each operator).
+ * fio_batch_create -- group n_ops built pairs (bfs[i], hss[i]); the HSS
+ *   handles must be factored.  The batch keeps pointers to the handles (they
+ *   must outlive it) and owns its workspaces.
+ * fio_batch_set_mode -- 0: one fio_solve per operator; 1: grouped launches
+ *   (each stage one launch over all operators: the two fused BF half passes,
+ *   one ULV node-product launch per tree depth, one for the roots); 2: the
+ *   grouped launches captured once into a CUDA graph and replayed (default).
+ * fio_batch_solve -- F[i] = G~_i^{-1} K~_i^* U[i] for every i: U, F host
+ *   arrays of n_ops device pointers to N_i x k[i] complex64 blocks with
+ *   leading dimension N_i (U[i] and F[i] must not overlap).  The launch plan
+ *   (device tables of arguments and work items; the graph) is built on the
+ *   first call for a given (U, F, k) and reused while they stay the same;
+ *   building it synchronizes the stream.
+ * fio_batch_autotune -- times each candidate configuration (per-operator
+ *   calls with the fused staged, fused unstaged or one-kernel-per-factor BF;
+ *   grouped launches; grouped launches in a graph) over `reps` solves on
+ *   the given buffers, keeps the fastest, and writes one line per candidate
+ *   ("name ms") into report (len bytes, may be NULL).
+ * ---------------------------------------------------------------------- */
+typedef struct fio_batch fio_batch;
+fio_status fio_batch_create(fio_bf* const* bfs, fio_hss* const* hss, int n_ops, fio_batch** out);
+fio_status fio_batch_set_mode(fio_batch* batch, int mode);
+fio_status fio_batch_solve(fio_batch* batch, const void* const* U, void* const* F, const int* k, void* stream);
+fio_status fio_batch_autotune(fio_batch* batch, const void* const* U, void* const* F, const int* k, int reps,
+                              void* stream, char* report, int64_t len);
+void fio_batch_free(fio_batch* batch);
+
 /* fio_last_error -- message of the last failing call on this thread. */
 const char* fio_last_error(void);
 

@@ -53,6 +53,12 @@ SIGNATURES = {
     "hss_solve": (I32, [P, P, P, I64, I32, P]),
     "fio_solve": (I32, [P, P, P, P, I64, I32, I32, P]),
     "hss_free": (None, [P]),
+    "fio_batch_create": (I32, [ctypes.POINTER(P), ctypes.POINTER(P), I32, PP]),
+    "fio_batch_set_mode": (I32, [P, I32]),
+    "fio_batch_solve": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I32), P]),
+    "fio_batch_autotune": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I32), I32, P,
+                                 ctypes.c_char_p, I64]),
+    "fio_batch_free": (None, [P]),
     "fio_last_error": (ctypes.c_char_p, []),
     "fio_profile_enable": (I32, [I32]),
     "fio_profile_report": (I32, [ctypes.c_char_p, I64]),

@@ -12,7 +12,7 @@ import torch
 from . import _lib
 from ._lib import FioError, check, lib
 
-__all__ = ["BF", "HSS", "fio_solve", "FioError"]
+__all__ = ["BF", "HSS", "Batch", "fio_solve", "FioError"]
 
 
 def _stream(stream=None):
@@ -166,3 +166,60 @@ def fio_solve(bf, hss, U, out=None, refine_steps=0, stream=None):
     check(lib.fio_solve(bf.handle, hss.handle, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k,
                         int(refine_steps), _stream(stream)))
     return out
+
+
+class Batch:
+    """Batched online solves over resident operators of uneven size (fio_batch_*).
+
+    ops: list of (BF, HSS) with factored HSS.  solve(Us) takes one (k_i, N_i)
+    complex64 CUDA tensor per operator and returns the solutions.
+    """
+
+    MODES = {"per_operator": 0, "grouped": 1, "graph": 2}
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        n = len(self.ops)
+        bfs = (ctypes.c_void_p * n)(*[b.handle.value for b, _ in self.ops])
+        hss = (ctypes.c_void_p * n)(*[h.handle.value for _, h in self.ops])
+        h = ctypes.c_void_p()
+        check(lib.fio_batch_create(bfs, hss, n, ctypes.byref(h)))
+        self._h = h
+
+    def set_mode(self, mode):
+        check(lib.fio_batch_set_mode(self._h, int(self.MODES.get(mode, mode))))
+        return self
+
+    def _arrays(self, Us, Fs):
+        n = len(self.ops)
+        if len(Us) != n or len(Fs) != n:
+            raise ValueError("one U and one F per operator")
+        ks = []
+        for (bf, _), U, F in zip(self.ops, Us, Fs):
+            pu, ld, k = _block(U, bf.n, "U")
+            pf, ldf, kf = _block(F, bf.n, "F")
+            if ld != bf.n or ldf != bf.n or kf != k:
+                raise ValueError("U and F must be contiguous (k, N) blocks of equal shape")
+            ks.append(k)
+        U_arr = (ctypes.c_void_p * n)(*[U.data_ptr() for U in Us])
+        F_arr = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
+        k_arr = (ctypes.c_int * n)(*ks)
+        return U_arr, F_arr, k_arr
+
+    def solve(self, Us, Fs=None, stream=None):
+        Fs = [torch.empty_like(U) for U in Us] if Fs is None else Fs
+        U_arr, F_arr, k_arr = self._arrays(Us, Fs)
+        check(lib.fio_batch_solve(self._h, U_arr, F_arr, k_arr, _stream(stream)))
+        return Fs
+
+    def autotune(self, Us, Fs, reps=3, stream=None):
+        U_arr, F_arr, k_arr = self._arrays(Us, Fs)
+        buf = ctypes.create_string_buffer(4096)
+        check(lib.fio_batch_autotune(self._h, U_arr, F_arr, k_arr, int(reps), _stream(stream), buf, len(buf)))
+        return buf.value.decode()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fio_batch_free(h)
+            self._h = ctypes.c_void_p()

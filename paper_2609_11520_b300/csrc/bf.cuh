@@ -45,9 +45,25 @@ struct fio_bf {
 namespace fio {
 // Fused two-pass apply (r = 16, L >= 6): middle state `mid` of N*r*kc complex.
 bool bf_fused_ok(const fio_bf* bf);
+bool bf_v3_ok(const fio_bf* bf);   // staged fused kernels apply (64..512 pairs per CTA)
 int bf_fused_kc(const fio_bf* bf);
 fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, float2* mid,
                           cudaStream_t st);
+// Grouped fused apply over several operators (bf_v3_ok each): host tables, then
+// launches that only read device copies of them.
+struct BfGroupOp {
+    const fio_bf* bf;
+    const float2* X;
+    float2* Y;
+    float2* mid;   // N r k complex
+    int k;
+};
+void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector<unsigned char>& left_args,
+                     std::vector<int4>& left_items, std::vector<unsigned char>& right_args,
+                     std::vector<int4>& right_items);
+size_t bf_group_args_size();
+fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
+                           const int4* dright_items, int nright, int adjoint, cudaStream_t st);
 // Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st);

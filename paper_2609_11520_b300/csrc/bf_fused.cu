@@ -21,6 +21,8 @@
 //   base = a 2^W + rev_(j-1)(s' mod 2^(j-1)) 2^(W-j) + (s' >> (j-1)).
 // Threads enumerate quads by physical slot, so that consecutive threads touch
 // consecutive slots, and shared memory is XOR-swizzled in 16-byte chunks.
+#include <cstring>
+
 #include "bf.cuh"
 
 namespace fio {
@@ -466,7 +468,7 @@ __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 struct Geo {
-    int L, h, sU, sV, n, P;
+    int L, h, sU, sV, n, P, lgP, KC;   // KC * P = NT
 };
 
 // Stage the phase slice of level s (contiguous in global memory) into `buf`.
@@ -513,13 +515,13 @@ __device__ void stage_m(float4* buf, const float2* __restrict__ M, int box, int 
     }
 }
 
-template <int KC, bool LEFT, bool MS, bool ADJ>
+template <bool LEFT, bool MS, bool ADJ>
 __device__ void level3(float2* S, const float* sPc, const float4* ph, int s, const Geo& g) {
     const int P = g.P;
     const int W = LEFT ? g.L - s : g.h - s;
     const int half = 1 << (W - 1);
-    const int id = threadIdx.x;   // KC * P == NT
-    const int col = id / P, rem = id - col * P, qi = rem >> 1, o = rem & 1;
+    const int id = threadIdx.x;   // KC * P == NT: one quad half per thread
+    const int col = id >> g.lgP, rem = id & (P - 1), qi = rem >> 1, o = rem & 1;
     const int base = ((qi >> (W - 1)) << W) | (qi & (half - 1));
     float2* Sc = S + col * P * R;
     float2 x0[R], x1[R];
@@ -602,11 +604,11 @@ __device__ void level3(float2* S, const float* sPc, const float4* ph, int s, con
 
 // One chunk of M (forward, RIGHT) or M^* (adjoint, LEFT), in place: task =
 // (pair of the chunk, column, output index), 16 lanes per (pair, column).
-template <int KC, bool LEFT>
+template <bool LEFT>
 __device__ void mchunk3(float2* S, const float4* mb, int ck, const Geo& g) {
     const int P = g.P, CH = P / 8;
     const int nB = g.sU - g.h, lo = g.L - g.sU;
-    const int ntask = CH * KC * R;
+    const int ntask = CH * g.KC * R;
     for (int b0 = 0; b0 < ntask; b0 += NT) {
         const int id = b0 + threadIdx.x;
         const bool act = id < ntask;
@@ -638,22 +640,60 @@ __device__ void mchunk3(float2* S, const float4* mb, int ck, const Geo& g) {
     }
 }
 
-template <int KC, bool ADJ>
-__global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
+// Shared-memory layout of one CTA: state (64 KiB), one or two table buffers
+// of P * 256 B (two when P <= 256: the next item is staged while the current
+// one is computed), the Lagrange matrices.
+__device__ __forceinline__ int nbuf3(int P) { return P <= 256 ? 2 : 1; }
+
+// Runs the staged item sequence: items [0, nlev) are transfer levels, the
+// rest middle-level chunks; `stage(it, buf)` issues the copies of item it,
+// `compute(it, buf)` consumes them.
+template <class StageF, class ComputeF>
+__device__ void pipeline3(int nitem, int P, float4* buf0, float4* buf1, StageF stage, ComputeF compute) {
+    if (nitem == 0) return;
+    if (nbuf3(P) == 2) {
+        for (int it = 0; it < nitem; ++it) {
+            float4* cur = (it & 1) ? buf1 : buf0;
+            if (it + 1 < nitem) {
+                stage(it + 1, (it & 1) ? buf0 : buf1);
+                cp_commit();
+                cp_wait1();
+            } else {
+                cp_wait0();
+            }
+            __syncthreads();
+            compute(it, cur);
+            __syncthreads();
+        }
+    } else {
+        for (int it = 0; it < nitem; ++it) {
+            if (it > 0) {
+                stage(it, buf0);
+                cp_commit();
+            }
+            cp_wait0();
+            __syncthreads();
+            compute(it, buf0);
+            __syncthreads();
+        }
+    }
+}
+
+template <bool ADJ>
+__device__ void left3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
-    Geo g{a.L, a.h, a.sU, a.sV, a.n, 1 << (a.L - a.h)};
-    const int P = g.P;
+    Geo g;
+    g.L = a.L; g.h = a.h; g.sU = a.sU; g.sV = a.sV; g.n = a.n;
+    g.lgP = a.L - a.h; g.P = 1 << g.lgP; g.KC = NT >> g.lgP;
+    const int P = g.P, KC = g.KC;
     float2* S = reinterpret_cast<float2*>(smem4);
-    float4* buf0 = smem4 + KC * P * R / 2;
+    float4* buf0 = smem4 + NT * R / 2;
     float4* buf1 = buf0 + P * 16;
-    float* sPc = reinterpret_cast<float*>(buf1 + P * 16);
+    float* sPc = reinterpret_cast<float*>(buf0 + nbuf3(P) * P * 16);
     float* sPU = sPc + 2 * PCS;
     const int lsU = 1 << (g.L - g.sU), nbU = lsU;
-    const int box = blockIdx.y, col0 = blockIdx.x * KC;
     const int kc = min(KC, a.k - col0);
     const int nlev = g.sU - g.h;
-    // item sequence: transfer levels (adjoint: sU-1 .. h; forward: h .. sU-1), then
-    // (adjoint only) the 8 chunks of M^*
     const int nitem = nlev + (ADJ ? 8 : 0);
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
@@ -661,6 +701,15 @@ __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
             stage_level<true, ADJ>(b, a.tab.t[s - g.h], box, s, g);
         } else {
             stage_m<true>(b, a.M, box, it - nlev, g);
+        }
+    };
+    auto compute = [&](int it, const float4* cur) {
+        if (it < nlev) {
+            const int s = ADJ ? g.sU - 1 - it : g.h + it;
+            if (ADJ) level3<true, false, true>(S, sPc, cur, s, g);
+            else level3<true, true, false>(S, sPc, cur, s, g);
+        } else {
+            mchunk3<true>(S, cur, it - nlev, g);
         }
     };
     if (nitem > 0) {
@@ -673,7 +722,7 @@ __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
     const int nB = nlev, lo = g.L - g.sU;
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U^*
-            const int col = id / P, lp = id - col * P;
+            const int col = id >> g.lgP, lp = id & (P - 1);
             if (col >= kc) continue;
             const int leaf = lp / nbU, b = lp - leaf * nbU;
             const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsU;
@@ -700,25 +749,7 @@ __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
             S[col * P * R + sw(slot, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i];
         }
     }
-    for (int it = 0; it < nitem; ++it) {
-        float4* cur = (it & 1) ? buf1 : buf0;
-        if (it + 1 < nitem) {
-            stage(it + 1, (it & 1) ? buf0 : buf1);
-            cp_commit();
-            cp_wait1();
-        } else {
-            cp_wait0();
-        }
-        __syncthreads();
-        if (it < nlev) {
-            const int s = ADJ ? g.sU - 1 - it : g.h + it;
-            if (ADJ) level3<KC, true, false, true>(S, sPc, cur, s, g);
-            else level3<KC, true, true, false>(S, sPc, cur, s, g);
-        } else {
-            mchunk3<KC, true>(S, cur, it - nlev, g);
-        }
-        __syncthreads();
-    }
+    pipeline3(nitem, P, buf0, buf1, stage, compute);
     if (ADJ) {
         for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
             const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
@@ -728,7 +759,7 @@ __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
         }
     } else {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U
-            const int col = id / P, xl = id - col * P;
+            const int col = id >> g.lgP, xl = id & (P - 1);
             if (col >= kc) continue;
             const int leaf = xl / lsU, qq = xl - leaf * lsU;
             const int64_t xg = int64_t(box) * P + xl;
@@ -751,22 +782,22 @@ __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
     }
 }
 
-template <int KC, bool ADJ>
-__global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
+template <bool ADJ>
+__device__ void right3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
-    Geo g{a.L, a.h, a.sU, a.sV, a.n, 1 << a.h};
-    const int P = g.P;
+    Geo g;
+    g.L = a.L; g.h = a.h; g.sU = a.sU; g.sV = a.sV; g.n = a.n;
+    g.lgP = a.h; g.P = 1 << g.lgP; g.KC = NT >> g.lgP;
+    const int P = g.P, KC = g.KC;
     float2* S = reinterpret_cast<float2*>(smem4);
-    float4* buf0 = smem4 + KC * P * R / 2;
+    float4* buf0 = smem4 + NT * R / 2;
     float4* buf1 = buf0 + P * 16;
-    float* sPc = reinterpret_cast<float*>(buf1 + P * 16);
+    float* sPc = reinterpret_cast<float*>(buf0 + nbuf3(P) * P * 16);
     float* sPV = sPc + 2 * PCS;
     const int lsV = 1 << g.sV, na = 1 << g.sV, nl = 1 << (g.h - g.sV);
-    const int box = blockIdx.y, col0 = blockIdx.x * KC;
     const int kc = min(KC, a.k - col0);
     const int64_t nmid = int64_t(1) << (g.L - g.h);
     const int nlev = g.h - g.sV;
-    // adjoint: C^* levels h-1 .. sV;  forward: C levels sV .. h-1, then 8 chunks of M
     const int nitem = nlev + (ADJ ? 0 : 8);
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
@@ -774,6 +805,15 @@ __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
             stage_level<false, ADJ>(b, a.tab.t[s - g.sV], box, s, g);
         } else {
             stage_m<false>(b, a.M, box, it - nlev, g);
+        }
+    };
+    auto compute = [&](int it, const float4* cur) {
+        if (it < nlev) {
+            const int s = ADJ ? g.h - 1 - it : g.sV + it;
+            if (ADJ) level3<false, true, true>(S, sPc, cur, s, g);
+            else level3<false, false, false>(S, sPc, cur, s, g);
+        } else {
+            mchunk3<false>(S, cur, it - nlev, g);
         }
     };
     if (nitem > 0) {
@@ -791,7 +831,7 @@ __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
         }
     } else {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // V
-            const int col = id / P, lp = id - col * P;
+            const int col = id >> g.lgP, lp = id & (P - 1);
             if (col >= kc) continue;
             const int aa = lp / nl, leaf = lp - aa * nl;
             const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsV;
@@ -811,28 +851,10 @@ __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
             store_pair(S + col * P * R, aa * nl + rev_bits(leaf, g.h - g.sV), y);
         }
     }
-    for (int it = 0; it < nitem; ++it) {
-        float4* cur = (it & 1) ? buf1 : buf0;
-        if (it + 1 < nitem) {
-            stage(it + 1, (it & 1) ? buf0 : buf1);
-            cp_commit();
-            cp_wait1();
-        } else {
-            cp_wait0();
-        }
-        __syncthreads();
-        if (it < nlev) {
-            const int s = ADJ ? g.h - 1 - it : g.sV + it;
-            if (ADJ) level3<KC, false, true, true>(S, sPc, cur, s, g);
-            else level3<KC, false, false, false>(S, sPc, cur, s, g);
-        } else {
-            mchunk3<KC, false>(S, cur, it - nlev, g);
-        }
-        __syncthreads();
-    }
+    pipeline3(nitem, P, buf0, buf1, stage, compute);
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // V^*
-            const int col = id / P, xl = id - col * P;
+            const int col = id >> g.lgP, xl = id & (P - 1);
             if (col >= kc) continue;
             const int leaf = xl >> g.sV, qq = xl & (lsV - 1);
             const int64_t xg = int64_t(box) * P + xl;
@@ -862,56 +884,141 @@ __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
     }
 }
 
-inline size_t smem3(int KC, int P) {
-    return size_t(KC) * P * R * 8 + size_t(2) * P * 256 + (2 * PCS + 8 * R) * sizeof(float);
+template <bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
+    left3_body<ADJ>(a, blockIdx.y, blockIdx.x * (NT >> (a.L - a.h)));
+}
+template <bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
+    right3_body<ADJ>(a, blockIdx.y, blockIdx.x * (NT >> a.h));
 }
 
-template <int KC, bool ADJ>
-fio_status launch_left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    const int P = 1 << (bf->L - bf->h);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_left3<KC, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
-    FIO_LAUNCH(ADJ ? "k_bf_left_adj" : "k_bf_left_fwd", st, k_left3<KC, ADJ><<<g, NT, smem3(KC, P), st>>>(a));
-    return FIO_OK;
+// Grouped launch over several operators: CTA b runs item items[b] =
+// (operator, box, first column) of the operators' half passes.
+template <bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_left3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    left3_body<ADJ>(args[it.x], it.y, it.z);
+}
+template <bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_right3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    right3_body<ADJ>(args[it.x], it.y, it.z);
 }
 
-template <int KC, bool ADJ>
-fio_status launch_right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    const int P = 1 << bf->h;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_right3<KC, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
-    FIO_LAUNCH(ADJ ? "k_bf_right_adj" : "k_bf_right_fwd", st, k_right3<KC, ADJ><<<g, NT, smem3(KC, P), st>>>(a));
-    return FIO_OK;
+inline size_t smem3(int P) {
+    return size_t(NT) * R * 8 + size_t(P <= 256 ? 2 : 1) * P * 256 + (2 * PCS + 8 * R) * sizeof(float);
+}
+constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + 8 * R) * sizeof(float);
+
+inline void set_attrs3() {
+    static bool done = false;
+    if (done) return;
+    const int mx = int(kSmem3Max);
+    cudaFuncSetAttribute(k_left3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    done = true;
 }
 
 template <bool ADJ>
 fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    switch (1 << (bf->L - bf->h)) {
-        case 64: return launch_left3<8, ADJ>(bf, a, kcols, st);
-        case 128: return launch_left3<4, ADJ>(bf, a, kcols, st);
-        default: return launch_left3<2, ADJ>(bf, a, kcols, st);
-    }
+    set_attrs3();
+    const int P = 1 << (bf->L - bf->h), KC = NT / P;
+    dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
+    FIO_LAUNCH(ADJ ? "k_bf_left_adj" : "k_bf_left_fwd", st, k_left3<ADJ><<<g, NT, smem3(P), st>>>(a));
+    return FIO_OK;
 }
 template <bool ADJ>
 fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    switch (1 << bf->h) {
-        case 64: return launch_right3<8, ADJ>(bf, a, kcols, st);
-        case 128: return launch_right3<4, ADJ>(bf, a, kcols, st);
-        default: return launch_right3<2, ADJ>(bf, a, kcols, st);
-    }
+    set_attrs3();
+    const int P = 1 << bf->h, KC = NT / P;
+    dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
+    FIO_LAUNCH(ADJ ? "k_bf_right_adj" : "k_bf_right_fwd", st, k_right3<ADJ><<<g, NT, smem3(P), st>>>(a));
+    return FIO_OK;
 }
 
 }  // namespace v3
 
 }  // namespace
+
+// ---------------------------------------------------------------- grouped
+// Host tables of a grouped half-pass launch over several operators.
+void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector<unsigned char>& left_args,
+                     std::vector<int4>& left_items, std::vector<unsigned char>& right_args,
+                     std::vector<int4>& right_items) {
+    left_args.assign(ops.size() * sizeof(HalfArgs), 0);
+    right_args.assign(ops.size() * sizeof(HalfArgs), 0);
+    left_items.clear();
+    right_items.clear();
+    for (size_t o = 0; o < ops.size(); ++o) {
+        const fio_bf* bf = ops[o].bf;
+        HalfArgs a{};
+        a.ldx = a.ldy = bf->n;
+        a.mid = ops[o].mid;
+        a.VP = bf->VP.as<float2>();
+        a.UP = bf->UP.as<float2>();
+        a.M = bf->M.as<float2>();
+        a.P = bf->P.as<float>();
+        a.pu_off = int(bf->pu_off());
+        a.pc_off = int(bf->pc_off());
+        a.n = bf->n;
+        a.L = bf->L;
+        a.h = bf->h;
+        a.sU = bf->sU;
+        a.sV = bf->sV;
+        a.k = ops[o].k;
+        HalfArgs al = a, ar = a;
+        for (size_t i = 0; i < bf->B.size() && i < 24; ++i) al.tab.t[i] = bf->B[i].as<float2>();
+        for (size_t i = 0; i < bf->C.size() && i < 24; ++i) ar.tab.t[i] = bf->C[i].as<float2>();
+        // adjoint: left reads X, writes mid; right reads mid, writes Y.  forward: the reverse.
+        if (adjoint) {
+            al.X = ops[o].X;
+            ar.Y = ops[o].Y;
+        } else {
+            ar.X = ops[o].X;
+            al.Y = ops[o].Y;
+        }
+        std::memcpy(left_args.data() + o * sizeof(HalfArgs), &al, sizeof(HalfArgs));
+        std::memcpy(right_args.data() + o * sizeof(HalfArgs), &ar, sizeof(HalfArgs));
+        const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
+        const int KCl = v3::NT / Pl, KCr = v3::NT / Pr;
+        for (int c0 = 0; c0 < ops[o].k; c0 += KCl)
+            for (int b = 0; b < (1 << bf->h); ++b) left_items.push_back(make_int4(int(o), b, c0, 0));
+        for (int c0 = 0; c0 < ops[o].k; c0 += KCr)
+            for (int b = 0; b < (1 << (bf->L - bf->h)); ++b) right_items.push_back(make_int4(int(o), b, c0, 0));
+    }
+}
+
+size_t bf_group_args_size() { return sizeof(HalfArgs); }
+
+// Launch the two grouped halves (device copies of the tables of bf_group_tables).
+fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
+                           const int4* dright_items, int nright, int adjoint, cudaStream_t st) {
+    v3::set_attrs3();
+    const HalfArgs* la = static_cast<const HalfArgs*>(dleft_args);
+    const HalfArgs* ra = static_cast<const HalfArgs*>(dright_args);
+    const size_t sm = v3::kSmem3Max;
+    if (adjoint) {
+        if (nleft) FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true><<<nleft, v3::NT, sm, st>>>(la, dleft_items));
+        if (nright) FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true><<<nright, v3::NT, sm, st>>>(ra, dright_items));
+    } else {
+        if (nright) FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false><<<nright, v3::NT, sm, st>>>(ra, dright_items));
+        if (nleft) FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false><<<nleft, v3::NT, sm, st>>>(la, dleft_items));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+bool bf_v3_ok(const fio_bf* bf) {
+    const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
+    return bf->r == R && Pl >= 64 && Pl <= 512 && Pr >= 64 && Pr <= 512;
+}
 
 bool bf_fused_ok(const fio_bf* bf) {
     if (bf->r != R || bf->L < 6) return false;
@@ -949,8 +1056,7 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
     Tabs tl{}, tr{};
     for (size_t i = 0; i < bf->B.size() && i < 24; ++i) tl.t[i] = bf->B[i].as<float2>();
     for (size_t i = 0; i < bf->C.size() && i < 24; ++i) tr.t[i] = bf->C[i].as<float2>();
-    const int Pl = 1 << (bf->L - bf->h), Pr = 1 << bf->h;
-    if (Pl >= 64 && Pl <= 256 && Pr >= 64 && Pr <= 256 && !bf->fused_v2) {
+    if (bf_v3_ok(bf) && !bf->fused_v2) {
         HalfArgs al = a, ar = a;
         al.tab = tl;
         ar.tab = tr;

@@ -32,4 +32,32 @@ void launch_expand(const float2* U, int nodes, int m, int r, const float2* in, i
                    int64_t ldout, int k, bool accumulate, cudaStream_t st);
 void launch_compress(const float2* U, int nodes, int m, int r, const float2* in, int64_t ldin, float2* out,
                      int64_t ldout, int k, cudaStream_t st);
+
+// The ULV solve as data: per level one node-product descriptor for the up
+// pass and one for the down pass, and the root product.
+struct UlvGemmDesc {
+    const float2* W;
+    const float2* inA;
+    const float2* inB;
+    float2* outC;
+    float2* outD;
+    int64_t ldA, ldB, ldC, ldD;
+    int m, nA, nC, k, nodes;
+};
+struct UlvRootDesc {
+    const float2* A;   // m x m
+    const float2* x;   // m x k (ld m)
+    float2* y;
+    int m, k;
+};
+struct UlvSolvePlan {
+    int Lh = 0;
+    std::vector<UlvGemmDesc> up, down;   // index = level l (1..Lh)
+    UlvRootDesc root{};
+};
+int64_t ulv_solve_ws_elems(const fio_hss* h, int k);
+fio_status ulv_solve_plan(fio_hss* h, const float2* B, float2* X, int64_t ld, int k, float2* ws, UlvSolvePlan& plan);
+void ulv_gemm_items(const UlvGemmDesc& d, int di, std::vector<int4>& items);
+fio_status ulv_group_launch(const UlvGemmDesc* dd, const int4* ditems, int nitems, bool down, cudaStream_t st);
+fio_status ulv_root_group_launch(const UlvRootDesc* dd, int n, cudaStream_t st);
 }

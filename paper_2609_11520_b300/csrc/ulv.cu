@@ -325,13 +325,12 @@ constexpr int WT = 32;
 constexpr int RB = 128;   // rows per CTA: 4 per thread
 
 template <bool CONJ>
-__global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
-                                                       int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
-                                                       float2* __restrict__ outC, int nC, int64_t ldC,
-                                                       float2* __restrict__ outD, int64_t ldD, int k) {
+__device__ void node_gemm_body(const float2* __restrict__ W, int m, const float2* __restrict__ inA, int nA, int64_t ldA,
+                               const float2* __restrict__ inB, int64_t ldB, float2* __restrict__ outC, int nC,
+                               int64_t ldC, float2* __restrict__ outD, int64_t ldD, int k, int t, int c0, int r0) {
     __shared__ float2 sx[WT * KCOL];       // sx[jj * KCOL + c]
     __shared__ float2 sw[WT * RB];         // sw[jj * RB + il]
-    const int t = blockIdx.x, c0 = blockIdx.y * KCOL, r0 = blockIdx.z * RB, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const int kc = min(KCOL, k - c0), nr = min(RB, m - r0);
     const float2* Wt = W + int64_t(t) * m * m;
     const int i0 = tid & 31, cg = tid >> 5;   // 8 column groups of 2
@@ -394,6 +393,36 @@ __global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict_
             if (i < nC) outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = acc[q][u];
             else outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[q][u];
         }
+    }
+}
+
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
+                                                       int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
+                                                       float2* __restrict__ outC, int nC, int64_t ldC,
+                                                       float2* __restrict__ outD, int64_t ldD, int k) {
+    node_gemm_body<CONJ>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k, blockIdx.x, blockIdx.y * KCOL,
+                         blockIdx.z * RB);
+}
+
+// Grouped node products: CTA b runs item (descriptor, node, first column, first row).
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_ulv_node_gemm_group(const UlvGemmDesc* __restrict__ d,
+                                                             const int4* __restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const UlvGemmDesc& g = d[it.x];
+    node_gemm_body<CONJ>(g.W, g.m, g.inA, g.nA, g.ldA, g.inB, g.ldB, g.outC, g.nC, g.ldC, g.outD, g.ldD, g.k, it.y,
+                         it.z, it.w);
+}
+
+// Grouped root products c = Rinv y, one CTA per descriptor.
+__global__ void k_root_group(const UlvRootDesc* __restrict__ d) {
+    const UlvRootDesc& g = d[blockIdx.x];
+    for (int e = threadIdx.x; e < g.m * g.k; e += blockDim.x) {
+        const int i = e % g.m, col = e / g.m;
+        float2 a = make_float2(0.f, 0.f);
+        for (int j = 0; j < g.m; ++j) cfma(a, g.A[i + int64_t(j) * g.m], g.x[int64_t(col) * g.m + j]);
+        g.y[int64_t(col) * g.m + i] = a;
     }
 }
 
@@ -581,3 +610,89 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
 }
+
+namespace fio {
+
+// Per-level vector layout of the solve (rows of the b^_1, y and c vectors).
+static int64_t solve_layout(const fio_hss* h, std::vector<int64_t>& ob, std::vector<int64_t>& oy, std::vector<int64_t>& oc) {
+    const int Lh = h->Lh;
+    ob.assign(Lh + 1, 0);
+    oy.assign(Lh + 1, 0);
+    oc.assign(Lh + 1, 0);
+    int64_t tot = 0;
+    for (int l = 0; l <= Lh; ++l) {
+        ob[l] = tot;
+        tot += (l >= 1) ? (int64_t(1) << l) * (h->m(l) - h->ranks[l]) : 0;
+        oy[l] = tot;
+        tot += (l < Lh) ? h->rows(l) : 0;
+        oc[l] = tot;
+        tot += (l < Lh) ? h->rows(l) : 0;
+    }
+    return tot;
+}
+
+int64_t ulv_solve_ws_elems(const fio_hss* h, int k) {
+    std::vector<int64_t> ob, oy, oc;
+    return std::max<int64_t>(2, solve_layout(h, ob, oy, oc) * k);
+}
+
+// The solve of one HSS handle as descriptors, on a caller-provided workspace
+// of ulv_solve_ws_elems(h, k) complex64 elements.
+fio_status ulv_solve_plan(fio_hss* h, const float2* B, float2* X, int64_t ld, int k, float2* w, UlvSolvePlan& plan) {
+    if (!h->factored) return fail(FIO_EINVAL, "ulv_solve_plan: call hss_ulv_factor first");
+    const int Lh = h->Lh;
+    std::vector<int64_t> ob, oy, oc;
+    solve_layout(h, ob, oy, oc);
+    auto bh = [&](int l) { return w + ob[l] * k; };
+    auto yv = [&](int l) { return w + oy[l] * k; };
+    auto cv = [&](int l) { return w + oc[l] * k; };
+    plan.up.assign(Lh + 1, UlvGemmDesc{});
+    plan.down.assign(Lh + 1, UlvGemmDesc{});
+    plan.Lh = Lh;
+    for (int l = Lh; l >= 1; --l) {
+        const int m = h->m(l), r = h->ranks[l];
+        UlvGemmDesc& u = plan.up[l];
+        UlvGemmDesc& d = plan.down[l];
+        u.nodes = d.nodes = (m == 0) ? 0 : (1 << l);
+        if (m == 0) continue;
+        const int64_t nb = (int64_t(1) << l) * (m - r);
+        const float2* in = (l == Lh) ? B : yv(l);
+        const int64_t ldin = (l == Lh) ? ld : h->rows(l);
+        u.W = d.W = h->W[l].as<float2>();
+        u.m = d.m = m;
+        u.k = d.k = k;
+        u.inA = in; u.nA = m; u.ldA = ldin; u.inB = in; u.ldB = ldin;
+        u.outC = bh(l); u.nC = m - r; u.ldC = std::max<int64_t>(nb, 1);
+        u.outD = yv(l - 1); u.ldD = std::max<int64_t>(h->rows(l - 1), 1);
+        float2* out = (l == Lh) ? X : cv(l);
+        const int64_t ldo = (l == Lh) ? ld : h->rows(l);
+        d.inA = bh(l); d.nA = m - r; d.ldA = std::max<int64_t>(nb, 1);
+        d.inB = cv(l - 1); d.ldB = std::max<int64_t>(h->rows(l - 1), 1);
+        d.outC = out; d.nC = m; d.ldC = ldo; d.outD = out; d.ldD = ldo;
+    }
+    plan.root = UlvRootDesc{h->Rinv.as<float2>(), yv(0), cv(0), 2 * h->ranks[1], k};
+    return FIO_OK;
+}
+
+void ulv_gemm_items(const UlvGemmDesc& d, int di, std::vector<int4>& items) {
+    for (int t = 0; t < d.nodes; ++t)
+        for (int c0 = 0; c0 < d.k; c0 += KCOL)
+            for (int r0 = 0; r0 < d.m; r0 += RB) items.push_back(make_int4(di, t, c0, r0));
+}
+
+fio_status ulv_group_launch(const UlvGemmDesc* dd, const int4* ditems, int nitems, bool down, cudaStream_t st) {
+    if (nitems == 0) return FIO_OK;
+    if (down) FIO_LAUNCH("k_ulv_down_group", st, k_ulv_node_gemm_group<true><<<nitems, 256, 0, st>>>(dd, ditems));
+    else FIO_LAUNCH("k_ulv_up_group", st, k_ulv_node_gemm_group<false><<<nitems, 256, 0, st>>>(dd, ditems));
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+fio_status ulv_root_group_launch(const UlvRootDesc* dd, int n, cudaStream_t st) {
+    if (n == 0) return FIO_OK;
+    FIO_LAUNCH("k_ulv_root_group", st, k_root_group<<<n, 256, 0, st>>>(dd));
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+}  // namespace fio

@@ -1,0 +1,85 @@
+"""Batched online solves over operators of uneven size (grouped launches, CUDA graph).
+
+Each mode must give the same solutions as one fio_solve per operator (same
+arithmetic, per-column independent), the graph replay must see in-place
+updates of its input buffers, and a new shape must replan.  fio_solve itself
+is checked against the oracle in test_gpu_hss.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+from fio_inputs import batched_operators, crandn
+from tests.gpu_util import rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_11520_b300 import BF, HSS
+    sizes = [(1 << 12, 0.55), (1 << 13, 0.8), (1 << 14, 0.95), (1 << 12, 0.7), (1 << 15, 0.6), (1 << 17, 1.0),
+             (1 << 11, 0.9)]
+    out = []
+    for i, (n, s) in enumerate(sizes):
+        bf = BF(n, 16, "cabs", s)
+        h = HSS.from_samples(bf=bf, leaf=128 if n >= 4096 else 64, oversample=10, tol=1e-3, seed=10 + i).factor()
+        out.append((bf, h))
+    return out
+
+
+def test_batch_modes_equal_per_operator(ops):
+    from paper_2609_11520_b300 import Batch, fio_solve
+    ks = [16, 5, 16, 1, 9, 3, 7]
+    Us = [to_dev(crandn(bf.n, k, seed=100 + i)) for i, ((bf, _), k) in enumerate(zip(ops, ks))]
+    refs = [to_np(fio_solve(bf, h, U)) for (bf, h), U in zip(ops, Us)]
+    b = Batch(ops)
+    for mode in ("per_operator", "grouped", "graph"):
+        b.set_mode(mode)
+        Fs = [torch.empty_like(U) for U in Us]
+        for rep in range(3):   # graph: eager + capture, then replays
+            b.solve(Us, Fs)
+        torch.cuda.synchronize()
+        for F, ref in zip(Fs, refs):
+            assert rel(to_np(F), ref) < 1e-5, mode
+
+
+def test_graph_replay_sees_new_inputs_and_replans(ops):
+    from paper_2609_11520_b300 import Batch, fio_solve
+    b = Batch(ops).set_mode("graph")
+    ks = [4] * len(ops)
+    Us = [to_dev(crandn(bf.n, k, seed=200 + i)) for i, ((bf, _), k) in enumerate(zip(ops, ks))]
+    Fs = [torch.empty_like(U) for U in Us]
+    b.solve(Us, Fs)
+    b.solve(Us, Fs)
+    for i, U in enumerate(Us):   # new data in the same buffers
+        U.copy_(to_dev(crandn(ops[i][0].n, 4, seed=300 + i)))
+    b.solve(Us, Fs)
+    torch.cuda.synchronize()
+    for (bf, h), U, F in zip(ops, Us, Fs):
+        assert rel(to_np(F), to_np(fio_solve(bf, h, U))) < 1e-5
+    Us2 = [to_dev(crandn(bf.n, 2, seed=400 + i)) for i, (bf, _) in enumerate(ops)]
+    Fs2 = b.solve(Us2)
+    torch.cuda.synchronize()
+    for (bf, h), U, F in zip(ops, Us2, Fs2):
+        assert rel(to_np(F), to_np(fio_solve(bf, h, U))) < 1e-5
+
+
+def test_autotune_reports_every_candidate(ops):
+    from paper_2609_11520_b300 import Batch
+    b = Batch(ops[:4])
+    Us = [to_dev(crandn(bf.n, 8, seed=500 + i)) for i, (bf, _) in enumerate(ops[:4])]
+    Fs = [torch.empty_like(U) for U in Us]
+    rep = b.autotune(Us, Fs, reps=2)
+    assert "grouped launches in a CUDA graph" in rep and "chosen:" in rep
+    b.solve(Us, Fs)
+
+
+def test_batched_workload_operators():
+    """The batched workload's operator list: 32 operators, N in 2^12..2^17, s in [0.5, 1]."""
+    ops_ = batched_operators()
+    assert len(ops_) == 32
+    assert {n for n, _ in ops_} <= {1 << e for e in range(12, 18)}
+    assert all(0.5 <= s <= 1.0 for _, s in ops_)
