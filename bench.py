@@ -459,6 +459,24 @@ def main():
     kernels = {name: {"launches": c, "ms_total": round(ms, 4), "share": round(ms / sum(v[1] for v in prof.values()), 4)}
                for name, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    # ---- split-precision transfer levels (BF16 hi + lo on the tensor cores), same served block ----
+    split = None
+    try:
+        bf.set_precision("split_bf16")
+    except Exception as e:   # operator shape without a split kernel
+        split = {"unavailable": str(e)}
+    if split is None:
+        sp = timed(lambda: fio_solve(bf, hss, U, out=OUT), args.steps, args.warmup)
+        e_sp = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+        sp1 = timed(lambda: fio_solve(bf, hss, U, out=OUT, refine_steps=1), args.steps, args.warmup)
+        e_sp1 = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+        bf.set_precision("fp32")
+        fp1 = timed(lambda: fio_solve(bf, hss, U, out=OUT, refine_steps=1), args.steps, args.warmup)
+        e_fp1 = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+        split = {"value": world * k * args.steps / (sum(sp) / 1e3), "unit": UNIT, "e_direct_vs_f_true": e_sp,
+                 "refine1": {"value": world * k * args.steps / (sum(sp1) / 1e3), "e_vs_f_true": e_sp1},
+                 "fp32_refine1": {"value": world * k * args.steps / (sum(fp1) / 1e3), "e_vs_f_true": e_fp1}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cv, cores, sample, _ = cpu_oracle_online(n, 3, 0, w["leaf"], r)
@@ -480,6 +498,7 @@ def main():
             "latency_ms": {"served_p50": percentile(served, 50), "served_p99": percentile(served, 99),
                            "plain_p50": percentile(plain, 50), "plain_p99": percentile(plain, 99)},
             "plain": {"value": plain_value, "unit": UNIT, "k_per_call": 1},
+            "split_bf16": split,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(U.numel() * 8),
                     "d2h_bytes_per_step": int(U.numel() * 8)},
             "gpu_launches": int(launches),

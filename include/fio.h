@@ -119,6 +119,15 @@ fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld
  *   without the staging.  FIO_EINVAL where a fused path is unsupported. */
 fio_status bf_set_path(fio_bf* bf, int path);
 
+/* bf_set_precision -- arithmetic of the transfer levels of bf_apply:
+ *   FIO_FP32 (0, default) FP32 FMA; FIO_SPLIT_BF16 (1) tensor-core products
+ *   on BF16 operands split as v = hi + lo (hi*hi + hi*lo + lo*hi, FP32
+ *   accumulation), phases and the middle factor in FP32; relative error of
+ *   an apply about 1e-5.  Split precision runs on the staged fused kernels
+ *   (r = 16, 2^12 <= n <= 2^18; FIO_EINVAL otherwise) whatever bf_set_path chose. */
+typedef enum { FIO_FP32 = 0, FIO_SPLIT_BF16 = 1 } fio_precision;
+fio_status bf_set_precision(fio_bf* bf, int precision);
+
 /* bf_info -- sizes of a handle: out[0..7] = n, d, r, L, h, sU (space level of
  *   U), sV (space level of V), bytes of device factor tables. */
 fio_status bf_info(const fio_bf* bf, int64_t* out8);
@@ -176,7 +185,9 @@ fio_status hss_ulv_factor(fio_hss* hss, void* stream);
 fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int k, void* stream);
 
 /* fio_solve -- online stage f = G~^{-1} K~^* u (Eq. 4.2), plus `refine_steps`
- *   steps of iterative refinement f += G~^{-1}(K~^* u - K~^* K~ f).
+ *   steps of iterative refinement f += G~^{-1}(K~^* u - K~^* K~ f) whose
+ *   residuals use the FP32 applies of K~ and K~^* (also for a handle set to
+ *   split precision).
  *   U, F: device, N x k complex64, ld >= N, no overlap. */
 fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
                      int refine_steps, void* stream);

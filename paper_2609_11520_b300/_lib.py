@@ -42,6 +42,7 @@ SIGNATURES = {
     "bf_apply": (I32, [P, P, P, I64, I32, I32, P]),
     "bf_info": (I32, [P, ctypes.POINTER(I64)]),
     "bf_set_path": (I32, [P, I32]),
+    "bf_set_precision": (I32, [P, I32]),
     "bf_apply_noalloc": (I32, [P, P, P, I64, I32, I32, P]),
     "bf_free": (None, [P]),
     "hss_build_from_samples": (I32, [ctypes.POINTER(Sampler), I64, I32, I32, ctypes.c_double, ctypes.c_uint64,

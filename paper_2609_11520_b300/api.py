@@ -52,6 +52,11 @@ class BF:
         check(lib.bf_set_path(self._h, int({"auto": 0, "per_level": 1, "fused": 2, "fused_v2": 3}.get(path, path))))
         return self
 
+    def set_precision(self, precision):
+        """"fp32" (default) or "split_bf16" (tensor-core transfer levels, BF16 hi + lo)."""
+        check(lib.bf_set_precision(self._h, int({"fp32": 0, "split_bf16": 1}.get(precision, precision))))
+        return self
+
     def info(self):
         o = (ctypes.c_int64 * 8)()
         check(lib.bf_info(self._h, o))

@@ -457,7 +457,7 @@ extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, i
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
     const int64_t stateN = int64_t(bf->n) * bf->r;
     cudaStream_t st = as_stream(stream);
-    const bool fused = bf_fused_ok(bf) && !bf->force_unfused;
+    const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || bf->split);
     // column chunk: at most 64 columns or 1 GiB of state, whichever is smaller
     const int nstate = fused ? 1 : 2;
     int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(1) << 30) / (nstate * stateN * 8)))));
@@ -479,6 +479,14 @@ extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
     if (path >= 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
     bf->force_unfused = (path == 1);
     bf->fused_v2 = (path == 3);
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_set_precision(fio_bf* bf, int precision) {
+    if (!bf || precision < 0 || precision > 1) return fail(FIO_EINVAL, "bf_set_precision: bad handle or precision");
+    if (precision == 1 && !bf_v3_ok(bf))
+        return fail(FIO_EINVAL, "bf_set_precision: split BF16 needs r = 16 and 2^12 <= n <= 2^18");
+    bf->split = (precision == 1);
     return FIO_OK;
 }
 

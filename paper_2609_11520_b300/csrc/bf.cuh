@@ -36,6 +36,7 @@ struct fio_bf {
     int64_t table_bytes = 0;
     bool force_unfused = false;    // use the per-level kernels even where the fused pass applies
     bool fused_v2 = false;         // fused pass without shared-memory table staging
+    bool split = false;            // transfer levels in split BF16 on the tensor cores (staged fused path)
     int64_t N() const { return int64_t(n); }
     size_t pv_off() const { return 0; }
     size_t pu_off() const { return size_t(lsV) * r; }
@@ -63,7 +64,7 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
                      std::vector<int4>& right_items);
 size_t bf_group_args_size();
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
-                           const int4* dright_items, int nright, int adjoint, cudaStream_t st);
+                           const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st);
 // Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st);

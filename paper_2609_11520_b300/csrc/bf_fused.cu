@@ -21,6 +21,8 @@
 //   base = a 2^W + rev_(j-1)(s' mod 2^(j-1)) 2^(W-j) + (s' >> (j-1)).
 // Threads enumerate quads by physical slot, so that consecutive threads touch
 // consecutive slots, and shared memory is XOR-swizzled in 16-byte chunks.
+#include <cuda_bf16.h>
+
 #include <cstring>
 
 #include "bf.cuh"
@@ -238,6 +240,7 @@ struct HalfArgs {
     int pu_off, pc_off;
     Tabs tab;            // left: E tables by s - h ; right: F tables by s - sV
     int n, L, h, sU, sV, k;
+    int split;           // transfer levels on the tensor cores, BF16 hi+lo (v3 kernels only)
 };
 
 // Left half, one CTA per space box tau_h (blockIdx.x) and KC columns (blockIdx.y).
@@ -602,6 +605,136 @@ __device__ void level3(float2* S, const float* sPc, const float4* ph, int s, con
     store_pair(Sc, o ? base + half : base, y);
 }
 
+// ---------------------------------------------------------------- split BF16
+// Transfer level on the tensor cores.  The real Lagrange products of a level
+// are GEMMs with a matrix shared by every quad:
+//   MS:  H_o = P_o X            (16 x 16) x (16 x columns), columns = (quad, e, re/im)
+//   SM:  Y_o = [P_0^T P_1^T] G_o (16 x 32) x (32 x columns), G = phase-scaled inputs
+// computed with mma.sync m16n8k16 on BF16 operands split as v = hi + lo
+// (three products hi*hi + hi*lo + lo*hi, FP32 accumulation); the complex phase
+// products stay in FP32.  A warp tile is two quads of one column: 8 GEMM
+// columns = 4 complex vectors.  Fragment coordinates (PTX m16n8k16): lane =
+// 4 g + t; A rows g, g+8 x cols 2t, 2t+1, 2t+8, 2t+9; B rows (k) 2t, 2t+1,
+// 2t+8, 2t+9 x col g; D rows g, g+8 x cols 2t, 2t+1.
+struct SplitFrag {
+    unsigned hi[4], lo[4];
+};
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // a in the low half
+    return *reinterpret_cast<unsigned*>(&v);
+}
+// hi / lo BF16 parts of a pair of floats
+__device__ __forceinline__ void split2(float a, float b, unsigned& hi, unsigned& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = *reinterpret_cast<const unsigned*>(&h);
+    lo = pack_bf16(a - hf.x, b - hf.y);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// A fragment of a 16 x 16 matrix given by elem(row, col)
+template <class F> __device__ __forceinline__ SplitFrag afrag(F elem) {
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    SplitFrag f;
+    split2(elem(g, 2 * t), elem(g, 2 * t + 1), f.hi[0], f.lo[0]);
+    split2(elem(g + 8, 2 * t), elem(g + 8, 2 * t + 1), f.hi[1], f.lo[1]);
+    split2(elem(g, 2 * t + 8), elem(g, 2 * t + 9), f.hi[2], f.lo[2]);
+    split2(elem(g + 8, 2 * t + 8), elem(g + 8, 2 * t + 9), f.hi[3], f.lo[3]);
+    return f;
+}
+__device__ __forceinline__ void mma3(float (&d)[4], const SplitFrag& a, unsigned bh0, unsigned bh1, unsigned bl0,
+                                     unsigned bl1) {
+    mma_bf16(d, a.hi, bh0, bh1);
+    mma_bf16(d, a.hi, bl0, bl1);
+    mma_bf16(d, a.lo, bh0, bh1);
+}
+__device__ __forceinline__ float2 chunk_elem(const float4* row, int sw8, int i) {
+    const float4 v = row[(i >> 1) ^ sw8];
+    return (i & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
+// fa[0..1]: MS -> P_0, P_1 (rows i, cols t);  SM -> P_0^T, P_1^T (rows j, cols t).
+template <bool LEFT, bool MS, bool ADJ>
+__device__ void level3_tc(float2* S, const SplitFrag (&fa)[2], const float4* ph, int s, const Geo& g) {
+    const int P = g.P;
+    const int W = LEFT ? g.L - s : g.h - s;
+    const int half = 1 << (W - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gg = lane >> 2, t = lane & 3;
+    const int ntile = (P / 4) * g.KC;
+    for (int tile = warp; tile < ntile; tile += NT / 32) {
+        const int col = tile / (P / 4), qp = tile % (P / 4);
+        float2* Sc = S + col * P * R;
+        auto basef = [&](int qi) { return ((qi >> (W - 1)) << W) | (qi & (half - 1)); };
+        // ---- B fragments (this lane's GEMM column gg: vector gg >> 1, part gg & 1)
+        const int v = gg >> 1, part = gg & 1;
+        const int qb = 2 * qp + (v >> 1);
+        const int vb = v & 1;   // MS: input half e; SM: output half o
+        const int bq = basef(qb);
+        unsigned bh[2][2], bl[2][2];   // [K step][register]
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (MS && e == 1) break;
+            const int slot = bq + (MS ? vb : e) * half;
+            float2 xv[4];
+            const int tt[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = Sc[sw(slot, tt[u])];
+            if (!MS) {   // phase-scale first: g = Phi(o, e, t) x[e][t]
+                const int row = qb * 4 + vb * 2 + e, sw8 = (qb * 2 + vb) & 7;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 f = chunk_elem(ph + row * 8, sw8, tt[u]);
+                    xv[u] = ADJ ? cmulc(f, xv[u]) : cmul(f, xv[u]);
+                }
+            }
+            float val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) val[u] = part ? xv[u].y : xv[u].x;
+            split2(val[0], val[1], bh[e][0], bl[e][0]);
+            split2(val[2], val[3], bh[e][1], bl[e][1]);
+        }
+        __syncwarp();
+        // ---- products; D columns 2t, 2t+1 = (re, im) of vector t
+        const int qd = 2 * qp + (t >> 1), vd = t & 1;
+        const int bd = basef(qd);
+        if (MS) {
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(d, fa[o], bh[0][0], bh[0][1], bl[0][0], bl[0][1]);
+                // h[o][e = vd][i] for i = gg, gg + 8; y[o][i] = sum_e Phi(o, e, i) h[o][e][i]
+                const int row = qd * 4 + o * 2 + vd, sw8 = (qd * 2 + o) & 7;
+                const float2 f0 = chunk_elem(ph + row * 8, sw8, gg), f1 = chunk_elem(ph + row * 8, sw8, gg + 8);
+                const float2 h0 = make_float2(d[0], d[1]), h1 = make_float2(d[2], d[3]);
+                float2 z0 = ADJ ? cmulc(f0, h0) : cmul(f0, h0);
+                float2 z1 = ADJ ? cmulc(f1, h1) : cmul(f1, h1);
+                z0.x += __shfl_xor_sync(0xffffffffu, z0.x, 1);
+                z0.y += __shfl_xor_sync(0xffffffffu, z0.y, 1);
+                z1.x += __shfl_xor_sync(0xffffffffu, z1.x, 1);
+                z1.y += __shfl_xor_sync(0xffffffffu, z1.y, 1);
+                if (vd == 0) {
+                    const int so = bd + o * half;
+                    Sc[sw(so, gg)] = z0;
+                    Sc[sw(so, gg + 8)] = z1;
+                }
+            }
+        } else {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            mma3(d, fa[0], bh[0][0], bh[0][1], bl[0][0], bl[0][1]);
+            mma3(d, fa[1], bh[1][0], bh[1][1], bl[1][0], bl[1][1]);
+            const int so = bd + vd * half;   // output half o = vd
+            Sc[sw(so, gg)] = make_float2(d[0], d[1]);
+            Sc[sw(so, gg + 8)] = make_float2(d[2], d[3]);
+        }
+    }
+}
+
 // One chunk of M (forward, RIGHT) or M^* (adjoint, LEFT), in place: task =
 // (pair of the chunk, column, output index), 16 lanes per (pair, column).
 template <bool LEFT>
@@ -679,7 +812,7 @@ __device__ void pipeline3(int nitem, int P, float4* buf0, float4* buf1, StageF s
     }
 }
 
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
     Geo g;
@@ -695,6 +828,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     const int kc = min(KC, a.k - col0);
     const int nlev = g.sU - g.h;
     const int nitem = nlev + (ADJ ? 8 : 0);
+    SplitFrag fa[2];
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
@@ -706,8 +840,13 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
-            if (ADJ) level3<true, false, true>(S, sPc, cur, s, g);
-            else level3<true, true, false>(S, sPc, cur, s, g);
+            if (SPLIT) {
+                if (ADJ) level3_tc<true, false, true>(S, fa, cur, s, g);
+                else level3_tc<true, true, false>(S, fa, cur, s, g);
+            } else {
+                if (ADJ) level3<true, false, true>(S, sPc, cur, s, g);
+                else level3<true, true, false>(S, sPc, cur, s, g);
+            }
         } else {
             mchunk3<true>(S, cur, it - nlev, g);
         }
@@ -719,6 +858,15 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[e] = a.P[a.pu_off + e];
     __syncthreads();
+    // split-precision A fragments: forward B levels are mix-then-scale (P_o), adjoint B^* scale-then-mix (P_e^T)
+    if (SPLIT) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float* Pm = sPc + c * PCS;
+            fa[c] = !ADJ ? afrag([&](int r_, int c_) { return Pm[r_ * R + c_]; })
+                         : afrag([&](int r_, int c_) { return Pm[c_ * R + r_]; });
+        }
+    }
     const int nB = nlev, lo = g.L - g.sU;
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U^*
@@ -782,7 +930,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     }
 }
 
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
     Geo g;
@@ -799,6 +947,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     const int64_t nmid = int64_t(1) << (g.L - g.h);
     const int nlev = g.h - g.sV;
     const int nitem = nlev + (ADJ ? 0 : 8);
+    SplitFrag fa[2];
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
@@ -810,8 +959,13 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
-            if (ADJ) level3<false, true, true>(S, sPc, cur, s, g);
-            else level3<false, false, false>(S, sPc, cur, s, g);
+            if (SPLIT) {
+                if (ADJ) level3_tc<false, true, true>(S, fa, cur, s, g);
+                else level3_tc<false, false, false>(S, fa, cur, s, g);
+            } else {
+                if (ADJ) level3<false, true, true>(S, sPc, cur, s, g);
+                else level3<false, false, false>(S, sPc, cur, s, g);
+            }
         } else {
             mchunk3<false>(S, cur, it - nlev, g);
         }
@@ -823,6 +977,15 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[e] = a.P[e];
     __syncthreads();
+    // split-precision A fragments: adjoint C^* levels are mix-then-scale (P_o), forward C scale-then-mix (P_e^T)
+    if (SPLIT) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float* Pm = sPc + c * PCS;
+            fa[c] = ADJ ? afrag([&](int r_, int c_) { return Pm[r_ * R + c_]; })
+                        : afrag([&](int r_, int c_) { return Pm[c_ * R + r_]; });
+        }
+    }
     if (ADJ) {
         for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
             const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
@@ -884,26 +1047,26 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     }
 }
 
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
-    left3_body<ADJ>(a, blockIdx.y, blockIdx.x * (NT >> (a.L - a.h)));
+    left3_body<ADJ, SPLIT>(a, blockIdx.y, blockIdx.x * (NT >> (a.L - a.h)));
 }
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
-    right3_body<ADJ>(a, blockIdx.y, blockIdx.x * (NT >> a.h));
+    right3_body<ADJ, SPLIT>(a, blockIdx.y, blockIdx.x * (NT >> a.h));
 }
 
 // Grouped launch over several operators: CTA b runs item items[b] =
 // (operator, box, first column) of the operators' half passes.
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1) k_left3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
     const int4 it = items[blockIdx.x];
-    left3_body<ADJ>(args[it.x], it.y, it.z);
+    left3_body<ADJ, SPLIT>(args[it.x], it.y, it.z);
 }
-template <bool ADJ>
+template <bool ADJ, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1) k_right3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
     const int4 it = items[blockIdx.x];
-    right3_body<ADJ>(args[it.x], it.y, it.z);
+    right3_body<ADJ, SPLIT>(args[it.x], it.y, it.z);
 }
 
 inline size_t smem3(int P) {
@@ -911,18 +1074,22 @@ inline size_t smem3(int P) {
 }
 constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + 8 * R) * sizeof(float);
 
+template <bool SPLIT> void set_attrs3_t() {
+    const int mx = int(kSmem3Max);
+    cudaFuncSetAttribute(k_left3<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3_group<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_left3_group<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3_group<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_right3_group<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
 inline void set_attrs3() {
     static bool done = false;
     if (done) return;
-    const int mx = int(kSmem3Max);
-    cudaFuncSetAttribute(k_left3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    set_attrs3_t<false>();
+    set_attrs3_t<true>();
     done = true;
 }
 
@@ -931,7 +1098,9 @@ fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st
     set_attrs3();
     const int P = 1 << (bf->L - bf->h), KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
-    FIO_LAUNCH(ADJ ? "k_bf_left_adj" : "k_bf_left_fwd", st, k_left3<ADJ><<<g, NT, smem3(P), st>>>(a));
+    const char* nm = ADJ ? "k_bf_left_adj" : "k_bf_left_fwd";
+    if (a.split) FIO_LAUNCH(nm, st, k_left3<ADJ, true><<<g, NT, smem3(P), st>>>(a));
+    else FIO_LAUNCH(nm, st, k_left3<ADJ, false><<<g, NT, smem3(P), st>>>(a));
     return FIO_OK;
 }
 template <bool ADJ>
@@ -939,7 +1108,9 @@ fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t s
     set_attrs3();
     const int P = 1 << bf->h, KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
-    FIO_LAUNCH(ADJ ? "k_bf_right_adj" : "k_bf_right_fwd", st, k_right3<ADJ><<<g, NT, smem3(P), st>>>(a));
+    const char* nm = ADJ ? "k_bf_right_adj" : "k_bf_right_fwd";
+    if (a.split) FIO_LAUNCH(nm, st, k_right3<ADJ, true><<<g, NT, smem3(P), st>>>(a));
+    else FIO_LAUNCH(nm, st, k_right3<ADJ, false><<<g, NT, smem3(P), st>>>(a));
     return FIO_OK;
 }
 
@@ -973,6 +1144,7 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
         a.sU = bf->sU;
         a.sV = bf->sV;
         a.k = ops[o].k;
+        a.split = bf->split ? 1 : 0;
         HalfArgs al = a, ar = a;
         for (size_t i = 0; i < bf->B.size() && i < 24; ++i) al.tab.t[i] = bf->B[i].as<float2>();
         for (size_t i = 0; i < bf->C.size() && i < 24; ++i) ar.tab.t[i] = bf->C[i].as<float2>();
@@ -999,17 +1171,30 @@ size_t bf_group_args_size() { return sizeof(HalfArgs); }
 
 // Launch the two grouped halves (device copies of the tables of bf_group_tables).
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
-                           const int4* dright_items, int nright, int adjoint, cudaStream_t st) {
+                           const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st) {
     v3::set_attrs3();
     const HalfArgs* la = static_cast<const HalfArgs*>(dleft_args);
     const HalfArgs* ra = static_cast<const HalfArgs*>(dright_args);
     const size_t sm = v3::kSmem3Max;
+    const int NT = v3::NT;
     if (adjoint) {
-        if (nleft) FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true><<<nleft, v3::NT, sm, st>>>(la, dleft_items));
-        if (nright) FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true><<<nright, v3::NT, sm, st>>>(ra, dright_items));
+        if (nleft) {
+            if (split) FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true, true><<<nleft, NT, sm, st>>>(la, dleft_items));
+            else FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true, false><<<nleft, NT, sm, st>>>(la, dleft_items));
+        }
+        if (nright) {
+            if (split) FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true, true><<<nright, NT, sm, st>>>(ra, dright_items));
+            else FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true, false><<<nright, NT, sm, st>>>(ra, dright_items));
+        }
     } else {
-        if (nright) FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false><<<nright, v3::NT, sm, st>>>(ra, dright_items));
-        if (nleft) FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false><<<nleft, v3::NT, sm, st>>>(la, dleft_items));
+        if (nright) {
+            if (split) FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false, true><<<nright, NT, sm, st>>>(ra, dright_items));
+            else FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false, false><<<nright, NT, sm, st>>>(ra, dright_items));
+        }
+        if (nleft) {
+            if (split) FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false, true><<<nleft, NT, sm, st>>>(la, dleft_items));
+            else FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false, false><<<nleft, NT, sm, st>>>(la, dleft_items));
+        }
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
@@ -1052,11 +1237,12 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
     a.sU = bf->sU;
     a.sV = bf->sV;
     a.k = kcols;
+    a.split = bf->split ? 1 : 0;
     // the left kernels read E tables (B levels), the right kernels F tables (C levels)
     Tabs tl{}, tr{};
     for (size_t i = 0; i < bf->B.size() && i < 24; ++i) tl.t[i] = bf->B[i].as<float2>();
     for (size_t i = 0; i < bf->C.size() && i < 24; ++i) tr.t[i] = bf->C[i].as<float2>();
-    if (bf_v3_ok(bf) && !bf->fused_v2) {
+    if (bf_v3_ok(bf) && (!bf->fused_v2 || bf->split)) {
         HalfArgs al = a, ar = a;
         al.tab = tl;
         ar.tab = tr;

@@ -1,6 +1,9 @@
 // Online stage of Algorithm 1: f = G~^{-1} K~^* u (Eq. 4.2), with optional
 // iterative refinement on the approximate normal equation (Eq. 4.3):
-//   f <- f + G~^{-1} (K~^* u - K~^* K~ f).
+//   f <- f + G~^{-1} (K~^* u - K~^* K~ f),
+// the residual always formed with the FP32 applies of K~ and K~^* (also when
+// the handle computes its applies in split BF16), so that the iteration
+// converges to the FP32 solution of Eq. 4.3 at a rate set by ||I - G~^{-1} K~^*K~||.
 #include "bf.cuh"
 #include "hss.cuh"
 
@@ -33,22 +36,37 @@ extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, vo
     fio_hss* h = const_cast<fio_hss*>(hc);
     cudaStream_t st = as_stream(stream);
     const int64_t N = h->N;
-    const int nbuf = refine_steps > 0 ? 3 : 1;
+    // buffers: T (K~^* u in the handle's precision), R1, R2 (refinement), T32 (FP32 K~^* u
+    // when the handle computes in split precision)
+    const bool split_refine = refine_steps > 0 && bf->split;
+    const int nbuf = refine_steps > 0 ? (split_refine ? 4 : 3) : 1;
     FIO_TRY(h->fio_ws.ensure(size_t(nbuf) * ld * k * 8));
     float2* T = h->fio_ws.as<float2>();
-    FIO_TRY(bf_apply(bf, U, T, ld, k, 1, st));                 // T = K~^* u (ld of the caller's block)
+    FIO_TRY(bf_apply(bf, U, T, ld, k, 1, st));                 // T = K~^* u
     FIO_TRY(hss_solve(h, T, F, ld, k, st));                    // f = G~^{-1} T
     if (refine_steps > 0) {
         float2* R1 = T + ld * k;
         float2* R2 = R1 + ld * k;
-        dim3 g(cdiv(N, 256), k);
-        for (int it = 0; it < refine_steps; ++it) {
-            FIO_TRY(bf_apply(bf, F, R1, ld, k, 0, st));        // K~ f
-            FIO_TRY(bf_apply(bf, R1, R2, ld, k, 1, st));       // K~^* K~ f
-            FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T, R2, R1, N, ld, ld, ld));   // residual of Eq. 4.3
-            FIO_TRY(hss_solve(h, R1, R2, ld, k, st));
-            FIO_LAUNCH("k_add", st, k_add<<<g, 256, 0, st>>>(static_cast<float2*>(F), R2, N, ld, ld));
+        // residuals of Eq. 4.3 against the FP32 applies of K~ and K~^*
+        const bool was_split = bf->split;
+        bf->split = false;
+        float2* T32 = T;
+        fio_status s = FIO_OK;
+        if (split_refine) {
+            T32 = R2 + ld * k;
+            s = bf_apply(bf, U, T32, ld, k, 1, st);
         }
+        dim3 g(cdiv(N, 256), k);
+        for (int it = 0; it < refine_steps && s == FIO_OK; ++it) {
+            s = bf_apply(bf, F, R1, ld, k, 0, st);                        // K~ f
+            if (s == FIO_OK) s = bf_apply(bf, R1, R2, ld, k, 1, st);      // K~^* K~ f
+            if (s != FIO_OK) break;
+            FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T32, R2, R1, N, ld, ld, ld));
+            s = hss_solve(h, R1, R2, ld, k, st);
+            if (s == FIO_OK) FIO_LAUNCH("k_add", st, k_add<<<g, 256, 0, st>>>(static_cast<float2*>(F), R2, N, ld, ld));
+        }
+        bf->split = was_split;
+        FIO_TRY(s);
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;

@@ -65,7 +65,7 @@ extern "C" fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y,
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply_noalloc: null vector");
     const int64_t stateN = int64_t(bf->n) * bf->r;   // one column of coefficient state
-    const bool fused = bf_fused_ok(bf) && !bf->force_unfused;
+    const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || bf->split);
     const int nstate = fused ? 1 : 2;
     if (nstate * stateN > kNoAllocScratchElems)
         return fail(FIO_EINVAL, "bf_apply_noalloc: one column needs " + std::to_string(nstate * stateN) +

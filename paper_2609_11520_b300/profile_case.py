@@ -10,6 +10,7 @@ captures only those launches.  Cases:
   bf_forward   Y = K~ X
   hss_solve    X = G~^{-1} B
   fio_solve    f = G~^{-1} K~^* u   (one online step)
+--precision split_bf16 runs the BF applies on the split-precision kernels.
 Prints the mean CUDA-event time per repetition.
 """
 import argparse
@@ -33,12 +34,14 @@ def main():
     ap.add_argument("--leaf", type=int, default=128)
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
     args = ap.parse_args()
     torch.cuda.set_device(0)
     bf = BF(args.n, args.r)
     hss = None
     if args.case in ("hss_solve", "fio_solve"):
         hss = HSS.from_samples(bf=bf, leaf=args.leaf, oversample=10, tol=args.tol, seed=2).factor()
+    bf.set_precision(args.precision)
     rng = np.random.default_rng(0)
     X = torch.from_numpy((rng.standard_normal((args.k, args.n)) + 1j * rng.standard_normal((args.k, args.n)))
                          .astype(np.complex64)).cuda()
