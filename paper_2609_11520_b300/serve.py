@@ -14,7 +14,10 @@ the device and runs a host loop that
   block of their operator (continuous batching);
 * copies the block's right-hand sides host->device, launches fio_solve on
   the slot's stream, copies the solutions back, and completes the requests
-  when the slot's event fires.
+  when the slot's event fires.  A request whose input (and output buffer,
+  if it brings one) is in pinned host memory is copied by one asynchronous
+  DMA per request straight into (out of) its columns of the block; other
+  requests go through the slot's pinned staging buffers.
 
 An operator has at most one block in flight (its handles are used by one
 stream at a time); blocks of different operators overlap on the device.
@@ -30,12 +33,13 @@ from .api import fio_solve
 
 
 class Request:
-    __slots__ = ("rid", "op", "k", "u", "f", "t_arrive", "t_admit", "t_done", "nbytes")
+    __slots__ = ("rid", "op", "k", "u", "f", "out", "t_arrive", "t_admit", "t_done", "nbytes")
 
-    def __init__(self, rid, op, u, t_arrive):
+    def __init__(self, rid, op, u, t_arrive, out=None):
         self.rid, self.op, self.u, self.t_arrive = rid, op, u, t_arrive
         self.k = u.shape[0]
         self.f = None
+        self.out = out
         self.t_admit = self.t_done = None
         self.nbytes = 2 * u.numel() * 8
 
@@ -56,6 +60,7 @@ class _Slot:
         self.reqs = []
         self.op = None
         self.out = None
+        self.direct_out = False
 
 
 class Server:
@@ -89,7 +94,12 @@ class Server:
                 now = time.perf_counter()
                 col = 0
                 for r in s.reqs:
-                    r.f = s.out[col:col + r.k].clone()
+                    if s.direct_out:
+                        r.f = r.out                         # written by the block's D2H copies
+                    elif r.out is not None:
+                        r.f = r.out.copy_(s.out[col:col + r.k])
+                    else:
+                        r.f = s.out[col:col + r.k].clone()
                     col += r.k
                     r.t_done = now
                     self.in_use -= r.nbytes
@@ -123,22 +133,39 @@ class Server:
                 F = torch.empty_like(U)
                 Hi = torch.empty(k, n, dtype=torch.complex64).pin_memory()
                 H = torch.empty(k, n, dtype=torch.complex64).pin_memory()
-            col = 0
-            for r in reqs:   # gather the block on the host (the slot is idle, so its buffers are free)
-                Hi[col:col + r.k].copy_(r.u)
-                col += r.k
+            direct_in = all(r.u.is_pinned() for r in reqs)
+            direct_out = all(r.out is not None and r.out.is_pinned() for r in reqs)
+            if not direct_in:
+                col = 0
+                for r in reqs:   # gather the block on the host (the slot is idle, so its buffers are free)
+                    Hi[col:col + r.k].copy_(r.u)
+                    col += r.k
             with torch.cuda.stream(s.stream):
-                U.copy_(Hi, non_blocking=True)
+                if direct_in:
+                    col = 0
+                    for r in reqs:
+                        U[col:col + r.k].copy_(r.u, non_blocking=True)
+                        col += r.k
+                else:
+                    U.copy_(Hi, non_blocking=True)
                 fio_solve(bf, hss, U, out=F, refine_steps=self.refine, stream=s.stream)
-                H.copy_(F, non_blocking=True)
+                if direct_out:
+                    col = 0
+                    for r in reqs:
+                        r.out.copy_(F[col:col + r.k], non_blocking=True)
+                        col += r.k
+                else:
+                    H.copy_(F, non_blocking=True)
                 s.event.record(s.stream)
-            s.out = H
+            s.out, s.direct_out = H, direct_out
             s.busy, s.reqs, s.op = True, reqs, name
             self.op_busy[name] = True
             self.blocks += 1
 
     def run(self, requests):
-        """Serve `requests` (list of (t_arrive_s, op_name, u host tensor (k, N))) in arrival order.
+        """Serve `requests` in arrival order: a list of (t_arrive_s, op_name, u) or
+        (t_arrive_s, op_name, u, out), u a host tensor (k, N) and out an optional host
+        tensor of the same shape that receives the solution.
 
         Returns the completed Request objects (results in .f, times in seconds
         relative to the start of the run).
@@ -149,8 +176,9 @@ class Server:
         while i < len(pending) or self.waiting or any(self.admitted.values()) or any(s.busy for s in self.slots):
             now = time.perf_counter() - t0
             while i < len(pending) and pending[i][0] <= now:
-                t, op, u = pending[i]
-                self.waiting.append(Request(i, op, u, t0 + t))
+                t, op, u = pending[i][:3]
+                out = pending[i][3] if len(pending[i]) > 3 else None
+                self.waiting.append(Request(i, op, u, t0 + t, out))
                 i += 1
             self._complete()
             self._admit()

@@ -65,3 +65,24 @@ def test_tight_hbm_budget_queues_and_completes(ops):
     assert srv.in_use == 0
     for r in done:
         assert r.f is not None and torch.isfinite(r.f).all()
+
+
+def test_pinned_outputs_and_pageable_inputs(ops):
+    """Requests that bring pinned output buffers get their solutions there (direct D2H per
+    request); pageable inputs go through the slot's staging buffers; both equal solving alone."""
+    from paper_2609_11520_b300 import fio_solve
+    from paper_2609_11520_b300.serve import Server
+    base = make_trace(ops, 40, rate=4000.0, seed=3)
+    reqs = []
+    for i, (t, name, u) in enumerate(base):
+        if i % 2:
+            reqs.append((t, name, u.clone(), torch.empty_like(u).pin_memory()))   # pageable in, pinned out
+        else:
+            reqs.append((t, name, u))
+    done = Server(ops, kmax=32, n_slots=2).run(reqs)
+    for r, req in zip(done, reqs):
+        bf, hss = ops[req[1]]
+        if len(req) > 3:
+            assert r.f is req[3]
+        alone = fio_solve(bf, hss, req[2].cuda()).cpu()
+        assert float(torch.linalg.norm(r.f - alone) / torch.linalg.norm(alone)) <= 1e-6
