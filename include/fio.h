@@ -48,8 +48,11 @@ typedef enum {
 } fio_status;
 
 typedef enum {
-    FIO_PHASE_DFT = 0,        /* Phi = x . xi  (then K^* K = N I exactly) */
-    FIO_PHASE_1D_CABS = 1     /* Phi = x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/16 */
+    FIO_PHASE_DFT = 0,        /* Phi = x . xi, d = 1 or 2  (then K^* K = N I exactly) */
+    FIO_PHASE_1D_CABS = 1,    /* d = 1: Phi = x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/16 */
+    FIO_PHASE_2D_ELLIPTIC = 2 /* d = 2: Phi = x . xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
+                                 c1 = (2 + sin 2 pi x1 sin 2 pi x2)/16,
+                                 c2 = (2 + cos 2 pi x1 cos 2 pi x2)/16 (Section 5.2) */
 } fio_phase_kind;
 
 typedef struct {
@@ -77,10 +80,14 @@ typedef struct {
 
 /* ------------------------------------------------------------------------
  * bf_build -- butterfly factorization K~ of K (Section 2.2, Eq. 2.1).
- *   n: points per dimension (power of two, 16 <= n <= 2^24); d: dimension
- *   (1); r: Chebyshev interpolation rank (1..32).  Trees: space/frequency
- *   dyadic trees of depth L = log2 n; middle level h = floor(L/2); outermost
- *   factors at max(L-3, h) (practical top level, Section 5.2).
+ *   n: points per dimension (power of two); d: dimension.
+ *   d = 1: 16 <= n <= 2^24, r: Chebyshev interpolation rank (1..16), N = n.
+ *   d = 2: 8 <= n <= 1024, r = 25 (5 x 5 tensor Chebyshev grid), N = n^2;
+ *     quadtrees, vectors in lexicographic order (x_i = (i1, i2)/n with
+ *     i = i1 n + i2, xi_j = (j1 - n/2, j2 - n/2) with j = j1 n + j2).
+ *   Trees: space/frequency trees of depth L = log2 n; middle level
+ *   h = floor(L/2); outermost factors at max(L-3, h) (practical top level,
+ *   Section 5.2).
  *   Every factor entry is evaluated on the device from its definition
  *   (phase differences in FP64, reduced mod 1, stored complex64).
  *   Synchronizes `stream` before returning.  *out receives the handle.
@@ -108,7 +115,8 @@ fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int a
  *   device looks up the array's device address (cudaGetSymbolAddress) with
  *   that device current: make it before any stream capture.  All calls share
  *   the array: calls whose GPU work overlaps race, so order them on one
- *   stream.  Arguments and errors as bf_apply. */
+ *   stream.  1D handles only (FIO_EINVAL for 2D).  Arguments and errors as
+ *   bf_apply. */
 fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream);
 
 /* bf_set_path -- choose the kernels of bf_apply (no paper counterpart; the
@@ -116,7 +124,8 @@ fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld
  *   where r = 16 and n >= 64, else per-level kernels), 1 = one kernel per
  *   factor (per-level), 2 = fused two-pass (tables staged through shared
  *   memory where each half has 64..256 pairs per CTA), 3 = fused two-pass
- *   without the staging.  FIO_EINVAL where a fused path is unsupported. */
+ *   without the staging.  FIO_EINVAL where a fused path is unsupported
+ *   (2D handles: per-level kernels only). */
 fio_status bf_set_path(fio_bf* bf, int path);
 
 /* bf_set_precision -- arithmetic of the transfer levels of bf_apply:
@@ -128,8 +137,9 @@ fio_status bf_set_path(fio_bf* bf, int path);
 typedef enum { FIO_FP32 = 0, FIO_SPLIT_BF16 = 1 } fio_precision;
 fio_status bf_set_precision(fio_bf* bf, int precision);
 
-/* bf_info -- sizes of a handle: out[0..7] = n, d, r, L, h, sU (space level of
- *   U), sV (space level of V), bytes of device factor tables. */
+/* bf_info -- sizes of a handle: out[0..7] = N (vector length n^d), d, r, L,
+ *   h, sU (space level of U), sV (space level of V), bytes of device factor
+ *   tables. */
 fio_status bf_info(const fio_bf* bf, int64_t* out8);
 
 void bf_free(fio_bf* bf);
@@ -147,6 +157,9 @@ void bf_free(fio_bf* bf);
  *   |R_kk| <= tol * max_j ||Y_tau(:,j)||, one rank per level (the level
  *   maximum), residual block D-check (Section 3.1), root H^[0] = Y^[0] Omega^+;
  *   top-down postprocessing for B and leaf D (Section 3.3).
+ *   FIO_SAMPLER_NORMAL with a 2D BF: the index set is the frequency grid in
+ *   quadtree (Morton) order, so that leaves and nodes are quadtree boxes and
+ *   their halves.
  *   Synchronizes `stream` (ranks are decided on the host).
  *   Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK.
  * ---------------------------------------------------------------------- */
@@ -188,7 +201,10 @@ fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int
  *   steps of iterative refinement f += G~^{-1}(K~^* u - K~^* K~ f) whose
  *   residuals use the FP32 applies of K~ and K~^* (also for a handle set to
  *   split precision).
- *   U, F: device, N x k complex64, ld >= N, no overlap. */
+ *   U, F: device, N x k complex64, ld >= N, no overlap.  2D handles: the HSS
+ *   (built by hss_build_from_samples from this BF) is over the frequency
+ *   index in quadtree (Morton) order; the solve runs in that order and F is
+ *   returned in lexicographic order. */
 fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
                      int refine_steps, void* stream);
 
@@ -198,8 +214,8 @@ void hss_free(fio_hss* hss);
  * Batched online stage over several resident operators of uneven size (the
  * batched workload: many independent 1D operators, a block of RHS each; no
  * paper counterpart beyond applying Eq. 4.2 to each operator).
- * fio_batch_create -- group n_ops built pairs (bfs[i], hss[i]); the HSS
- *   handles must be factored.  The batch keeps pointers to the handles (they
+ * fio_batch_create -- group n_ops built pairs (bfs[i], hss[i]) of 1D
+ *   operators (FIO_EINVAL for a 2D one); the HSS handles must be factored.  The batch keeps pointers to the handles (they
  *   must outlive it) and owns its workspaces.
  * fio_batch_set_mode -- 0: one fio_solve per operator; 1: grouped launches
  *   (each stage one launch over all operators: the two fused BF half passes,

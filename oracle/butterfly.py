@@ -69,7 +69,7 @@ def lagrange(nodes, x):
 class Butterfly1D:
     """BF of the 1D FIO with amplitude 1 (Eq. 2.1), applied block by block."""
 
-    def __init__(self, phase, n, r, max_block_elems=1 << 23, cache=None):
+    def __init__(self, phase, n, r, max_block_elems=1 << 23, cache=None, levels=None):
         L = int(round(np.log2(n)))
         if 2 ** L != n or L < 2:
             raise ValueError("n must be a power of two >= 4")
@@ -77,6 +77,10 @@ class Butterfly1D:
         self.h = L // 2
         self.sU = max(L - 3, self.h)
         self.sV = min(3, self.h)
+        if levels is not None:   # (h, sU, sV) other than Section 5.2's choice, 0 <= sV <= h <= sU <= L
+            self.h, self.sU, self.sV = levels
+            if not 0 <= self.sV <= self.h <= self.sU <= L:
+                raise ValueError("levels must satisfy 0 <= sV <= h <= sU <= L")
         self.t = cheb_nodes(r)
         self.max_block_elems = max_block_elems
         # Factor blocks are pure functions of (factor, level, chunk); keeping

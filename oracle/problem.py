@@ -18,12 +18,17 @@ import numpy as np
 
 
 class Phase:
-    def __init__(self, kind="cabs", s=1.0):
+    """Phase function of one workload family.  d is the dimension: 1 for
+    'cabs', 2 for 'elliptic2d', either for 'dft' (default 1)."""
+
+    def __init__(self, kind="cabs", s=1.0, d=None):
         if kind not in ("dft", "cabs", "elliptic2d"):
             raise ValueError(kind)
         self.kind = kind
         self.s = float(s)
-        self.d = 2 if kind == "elliptic2d" else 1
+        self.d = 2 if kind == "elliptic2d" else (1 if d is None else int(d))
+        if (kind == "cabs" and self.d != 1) or self.d not in (1, 2):
+            raise ValueError("phase %s has no %d-dimensional form" % (kind, self.d))
 
     def c(self, x):
         """c(x) of the 1D family."""
@@ -66,3 +71,44 @@ def K_rows(phase, n, rows):
     x = space_grid_1d(n)[np.asarray(rows)]
     xi = freq_grid_1d(n)
     return np.exp(2j * np.pi * phase(x[:, None], xi[None, :]))
+
+
+def space_grid_2d(n):
+    """x_i = (i1/n, i2/n) for the lexicographic index i = i1 n + i2 (i1 slow), shape (n^2, 2)."""
+    i1, i2 = np.divmod(np.arange(n * n), n)
+    return np.stack([i1 / n, i2 / n], axis=-1).astype(np.float64)
+
+
+def freq_grid_2d(n):
+    """xi_j = (j1 - n/2, j2 - n/2) for j = j1 n + j2 (j1 slow), shape (n^2, 2)."""
+    j1, j2 = np.divmod(np.arange(n * n), n)
+    return np.stack([j1 - n / 2, j2 - n / 2], axis=-1).astype(np.float64)
+
+
+def dense_K2(phase, n):
+    """Dense K (2D), Eq. 1.2 with a = 1, lexicographic rows and columns.  Small n only."""
+    x = space_grid_2d(n)
+    xi = freq_grid_2d(n)
+    return np.exp(2j * np.pi * phase(x[:, None, :], xi[None, :, :]))
+
+
+def K2_rows(phase, n, rows):
+    """Selected rows of the 2D K, entry by entry from Eq. 1.2."""
+    x = space_grid_2d(n)[np.asarray(rows)]
+    xi = freq_grid_2d(n)
+    return np.exp(2j * np.pi * phase(x[:, None, :], xi[None, :, :]))
+
+
+def morton_order(n):
+    """Quadtree (Morton) order of the n x n frequency grid: perm[m] is the
+    lexicographic index j = j1 n + j2 at Morton position m, where m interleaves
+    the bits of j1 (odd positions, more significant) and j2 (even positions).
+    Every quadtree box is then a contiguous range of positions."""
+    L = int(round(np.log2(n)))
+    m = np.arange(n * n)
+    j1 = np.zeros_like(m)
+    j2 = np.zeros_like(m)
+    for k in range(L):
+        j2 |= ((m >> (2 * k)) & 1) << k
+        j1 |= ((m >> (2 * k + 1)) & 1) << k
+    return j1 * n + j2

@@ -26,5 +26,34 @@ class FIOSolver:
         return self.ulv.solve(self.bf.adjoint(u))
 
 
+class FIOSolver2D:
+    """Algorithm 1 in 2D: the HSS of G~ = K~^* K~ is built over the frequency
+    index in quadtree (Morton) order, so that HSS leaves and nodes are
+    quadtree boxes and their concatenations (a binary tree whose levels
+    alternate the split direction); f^ = P^T F~ P K~^* u."""
+
+    def __init__(self, phase, n, r1, leaf, p, tol, seed, rank_frac=0.5):
+        from .butterfly2d import Butterfly2D
+        from .problem import morton_order
+        self.bf = Butterfly2D(phase, n, r1)
+        self.perm = morton_order(n)
+        self.stats = {}
+        N = n * n
+
+        def apply_H(X):   # P K~^* K~ P^T X
+            Y = np.empty_like(X)
+            Y[self.perm] = X
+            return self.bf.adjoint(self.bf.apply(Y))[self.perm]
+
+        self.hss = build_blackbox(apply_H, N, leaf, p, tol, seed, rank_frac=rank_frac, stats=self.stats)
+        self.ulv = ULV(self.hss)
+
+    def solve(self, u):
+        z = self.ulv.solve(self.bf.adjoint(u)[self.perm])
+        f = np.empty_like(z)
+        f[self.perm] = z
+        return f
+
+
 def rel_err(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libfio_b300.so")
 FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ENOTHPD, FIO_ERANK, FIO_ETIMEOUT, FIO_EBUSY = range(8)
 STATUS_NAMES = ["FIO_OK", "FIO_EINVAL", "FIO_ENOMEM", "FIO_ECUDA", "FIO_ENOTHPD", "FIO_ERANK",
                 "FIO_ETIMEOUT", "FIO_EBUSY"]
-PHASE_KINDS = {"dft": 0, "cabs": 1}
+PHASE_KINDS = {"dft": 0, "cabs": 1, "elliptic2d": 2}
 SAMPLER_NORMAL, SAMPLER_DENSE = 0, 1
 
 

@@ -34,14 +34,21 @@ def _block(x, n, name):
 
 
 class BF:
-    """Butterfly factorization K~ of the 1D FIO (bf_build / bf_apply)."""
+    """Butterfly factorization K~ of the FIO (bf_build / bf_apply).
 
-    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None):
+    n points per dimension; d = 2 for the "elliptic2d" phase (and for "dft"
+    when asked), else 1.  Vectors have length N = n^d (lexicographic in 2D)
+    and are held as (k, N) complex64 CUDA tensors; `self.n` is N.
+    """
+
+    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None, d=None):
+        d = (2 if phase == "elliptic2d" else 1) if d is None else int(d)
         ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
         h = ctypes.c_void_p()
-        check(lib.bf_build(ctypes.byref(ph), int(n), 1, int(r), _stream(stream), ctypes.byref(h)))
+        check(lib.bf_build(ctypes.byref(ph), int(n), d, int(r), _stream(stream), ctypes.byref(h)))
         self._h = h
-        self.n, self.r, self.phase, self.s = int(n), int(r), phase, float(s)
+        self.n_side, self.d = int(n), d
+        self.n, self.r, self.phase, self.s = int(n) ** d, int(r), phase, float(s)
 
     @property
     def handle(self):

@@ -190,6 +190,7 @@ extern "C" fio_status fio_batch_create(fio_bf* const* bfs, fio_hss* const* hss, 
         if (!bfs[i] || !hss[i]) return fail(FIO_EINVAL, "fio_batch_create: null operator");
         if (bfs[i]->N() != hss[i]->N) return fail(FIO_EINVAL, "fio_batch_create: BF and HSS sizes differ");
         if (!hss[i]->factored) return fail(FIO_EINVAL, "fio_batch_create: HSS not factored");
+        if (bfs[i]->d != 1) return fail(FIO_EINVAL, "fio_batch_create: 1D operators only (2D: fio_solve)");
     }
     fio_batch* b = new fio_batch();
     b->bfs.assign(bfs, bfs + n_ops);

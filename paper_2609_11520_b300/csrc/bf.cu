@@ -329,6 +329,8 @@ __global__ void k_quad(const float2* __restrict__ Sin, float2* __restrict__ Sout
     }
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------- host helpers
 double lagrange_host(const double* t, int r, int k, double u) {
     double v = 1.0;
@@ -336,8 +338,6 @@ double lagrange_host(const double* t, int r, int k, double u) {
         if (kk != k) v *= (u - t[kk]) / (t[k] - t[kk]);
     return v;
 }
-
-}  // namespace
 
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st) {
@@ -389,7 +389,27 @@ using namespace fio;
 extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, fio_bf** out) {
     if (!out || !phase) return fail(FIO_EINVAL, "bf_build: null pointer");
     *out = nullptr;
-    if (d != 1) return fail(FIO_EINVAL, "bf_build: only d = 1 is supported");
+    if (d == 2) {
+        const int L2 = ilog2_exact(n);
+        if (L2 < 3 || L2 > 10) return fail(FIO_EINVAL, "bf_build: 2D needs n a power of two in [8, 1024]");
+        if (r != 25) return fail(FIO_EINVAL, "bf_build: 2D needs r = 25 (5 x 5 tensor Chebyshev grid)");
+        if (!bf2d_ok_kind(phase->kind)) return fail(FIO_EINVAL, "bf_build: 2D phase must be DFT or 2D elliptic");
+        fio_bf* bf = new fio_bf();
+        bf->phase = *phase;
+        bf->nside = n; bf->n = n * n; bf->d = 2; bf->r = r; bf->L = L2;
+        bf->h = L2 / 2;
+        bf->sU = std::max(L2 - 3, bf->h);
+        bf->sV = std::min(3, bf->h);
+        fio_status s2 = bf2d_build(bf, as_stream(stream));
+        if (s2 != FIO_OK) {
+            bf_free(bf);
+            return s2;
+        }
+        *out = bf;
+        return FIO_OK;
+    }
+    if (d != 1) return fail(FIO_EINVAL, "bf_build: d must be 1 or 2");
+    if (phase->kind == FIO_PHASE_2D_ELLIPTIC) return fail(FIO_EINVAL, "bf_build: the elliptic phase is 2D (d = 2)");
     int L = ilog2_exact(n);
     if (L < 4 || L > 24) return fail(FIO_EINVAL, "bf_build: n must be a power of two in [16, 2^24]");
     if (r < 1 || r > kMaxR) return fail(FIO_EINVAL, "bf_build: r must be in [1, 16]");
@@ -398,7 +418,7 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
     cudaStream_t st = as_stream(stream);
     fio_bf* bf = new fio_bf();
     bf->phase = *phase;
-    bf->n = n; bf->d = d; bf->r = r; bf->L = L;
+    bf->n = n; bf->nside = n; bf->d = d; bf->r = r; bf->L = L;
     bf->h = L / 2;
     bf->sU = std::max(L - 3, bf->h);
     bf->sV = std::min(3, bf->h);
@@ -450,13 +470,36 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
     return FIO_OK;
 }
 
+namespace fio {
+fio_status bf_apply_ord(fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
+                        cudaStream_t st) {
+    if (!bf) return fail(FIO_EINVAL, "bf_apply: null handle");
+    if (bf->d == 1) return bf_apply(bf, X, Y, ld, k, adjoint, st);
+    if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
+    if (k == 0) return FIO_OK;
+    if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
+    const int64_t stateN = int64_t(bf->n) * bf->r;
+    const int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(32, (int64_t(1) << 30) / (2 * stateN * 8)))));
+    FIO_TRY(bf->ws.ensure(size_t(2) * stateN * kc * 8));
+    float2* s0 = bf->ws.as<float2>();
+    float2* s1 = s0 + stateN * kc;
+    for (int c0 = 0; c0 < k; c0 += kc) {
+        const int cc = std::min(kc, k - c0);
+        FIO_TRY(bf2d_apply_cols(bf, X + c0 * ld, Y + c0 * ld, ld, cc, adjoint, morton, s0, s1, st));
+    }
+    return FIO_OK;
+}
+}  // namespace fio
+
 extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream) {
     if (!bf) return fail(FIO_EINVAL, "bf_apply: null handle");
     if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
-    const int64_t stateN = int64_t(bf->n) * bf->r;
     cudaStream_t st = as_stream(stream);
+    if (bf->d == 2)
+        return bf_apply_ord(bf, static_cast<const float2*>(X), static_cast<float2*>(Y), ld, k, adjoint, false, st);
+    const int64_t stateN = int64_t(bf->n) * bf->r;
     const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || bf->split);
     // column chunk: at most 64 columns or 1 GiB of state, whichever is smaller
     const int nstate = fused ? 1 : 2;
@@ -476,6 +519,7 @@ extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, i
 
 extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
     if (!bf || path < 0 || path > 3) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
+    if (bf->d == 2 && path >= 2) return fail(FIO_EINVAL, "bf_set_path: 2D handles run the per-level kernels only");
     if (path >= 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
     bf->force_unfused = (path == 1);
     bf->fused_v2 = (path == 3);

@@ -26,7 +26,8 @@
 
 struct fio_bf {
     fio_phase phase;
-    int n = 0, d = 1, r = 0, L = 0, h = 0, sU = 0, sV = 0;
+    int n = 0, d = 1, r = 0, L = 0, h = 0, sU = 0, sV = 0;   // n: vector length N (n^d)
+    int nside = 0;                 // points per dimension; L = log2 nside
     int lsV = 0, lsU = 0;          // points per V frequency leaf / per U space leaf
     double tcheb[32];              // Chebyshev points on [-1, 1]
     fio::DevBuf VP, UP, M, P;      // P: PV | PU | Pc (float)
@@ -65,6 +66,19 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
 size_t bf_group_args_size();
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
                            const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st);
+// Host Lagrange polynomial l_k(u) on the nodes t[0..r).
+double lagrange_host(const double* t, int r, int k, double u);
+// 2D handles (d = 2, r = 25; bf2d.cu).  The same fio_bf fields hold the 2D
+// tables: VP, UP, M, C (F_s), B (E_s) and P (Pc | Pc^T | QV | QU).
+bool bf2d_ok_kind(int kind);
+fio_status bf2d_build(fio_bf* bf, cudaStream_t st);
+fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool morton,
+                           float2* s0, float2* s1, cudaStream_t st);
+fio_status bf2d_unmorton(const fio_bf* bf, const float2* Xm, float2* X, int64_t ld, int k, cudaStream_t st);
+// bf_apply with the frequency vectors of a 2D handle in quadtree (Morton)
+// order when `morton` is set (the order of the HSS of K~^* K~); 1D: bf_apply.
+fio_status bf_apply_ord(fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
+                        cudaStream_t st);
 // Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st);

@@ -1,0 +1,581 @@
+// Butterfly factorization of a 2D FIO (Section 2.2 with d = 2, Section 5.2):
+// quadtree boxes, tensor Chebyshev grids of r1 x r1 = 25 nodes, the same
+// factor sequence as Eq. 2.1.
+//
+// Geometry (per dimension as in 1D).  n points per dimension, N = n^2,
+// L = log2 n, h = floor(L/2), sU = max(L-3, h), sV = min(3, h).  A box at
+// level s is (a1, a2) with id a = a1 2^s + a2; its children are
+// (2 a1 + c1, 2 a2 + c2), child number c = 2 c1 + c2.  Node t = t1 r1 + t2 of
+// a box is the tensor product of the 1D first-kind Chebyshev points.  A pair
+// at space level s is (tau at space level s, sigma at frequency level L-s),
+// index tau 4^(L-s) + sigma.  Vectors are lexicographic (x_i = (i1, i2)/n
+// with i = i1 n + i2; xi_j = (j1 - n/2, j2 - n/2) with j = j1 n + j2); the
+// frequency side can instead be taken in quadtree (Morton) order, the order
+// in which the HSS of K~^* K~ is built.
+//
+// Phase-folded factored tables, as in 1D (the state between stages carries
+// e^{+2 pi i Phi(y_tau, gamma_sigma_j)} on the right side and
+// e^{-2 pi i Phi(z_tau_i, eta_sigma)} on the left side):
+//   VP[a][j]          e^{2 pi i Phi(y_a, xi_j)}                      a at level sV
+//   F_s[g][o][c][t]   e^{2 pi i (Phi(y_tau_o, gamma_beta_c,t) - Phi(y_tau, gamma_beta_c,t))}   C level s
+//   M[p][i][j]        e^{2 pi i (Phi(z_i, gamma_j) - Phi(z_i, eta) - Phi(y, gamma_j))}
+//   E_s[g][o][c][i]   e^{2 pi i (Phi(z_tau_o,i, eta_beta_c) - Phi(z_tau_o,i, eta_sigma'))}      B level s
+//   UP[x][b]          e^{2 pi i Phi(x, eta_b)}                       b at frequency level L-sU
+// with the group g = (tau at space level s, sigma' at frequency level L-s-1):
+// the inputs are the pairs (tau, beta_c = child c of sigma'), the outputs the
+// pairs (tau_o = child o of tau, sigma').  Real tables: Pc[c][j][t] =
+// l_j(child c node t) (the parent's Lagrange basis at a child's nodes; the
+// same matrix serves the frequency boxes of C and the space boxes of B),
+// its transpose, and the leaf bases QV[t][q], QU[x][i].
+#include <cmath>
+#include <cstring>
+
+#include "bf.cuh"
+
+namespace fio {
+namespace {
+
+constexpr int R1 = 5;
+constexpr int R = R1 * R1;      // 25
+constexpr int RP = 28;          // padded row of a real 25-vector (seven float4)
+constexpr int TB = 256;
+
+struct Cheb5 {
+    double t[R1];
+};
+
+// Phi(x, xi) of the 2D families (Section 5.2; Phi = x . xi for the DFT).
+__device__ __forceinline__ double phi2(int kind, double x1, double x2, double k1, double k2) {
+    double v = x1 * k1 + x2 * k2;
+    if (kind == FIO_PHASE_2D_ELLIPTIC) {
+        const double c1 = (2.0 + sinpi(2.0 * x1) * sinpi(2.0 * x2)) * 0.0625;
+        const double c2 = (2.0 + cospi(2.0 * x1) * cospi(2.0 * x2)) * 0.0625;
+        v += sqrt(c1 * c1 * k1 * k1 + c2 * c2 * k2 * k2);
+    }
+    return v;
+}
+
+// e^{2 pi i ph}: reduce modulo 1 in FP64, then sin/cos of the remainder.
+__device__ __forceinline__ float2 expi(double ph) {
+    const double fr = ph - rint(ph);
+    float sn, cs;
+    sincospif(2.0f * float(fr), &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+__host__ __device__ __forceinline__ int64_t child_id(int s, int64_t a, int c) {
+    const int64_t a1 = a >> s, a2 = a & ((int64_t(1) << s) - 1);
+    return ((2 * a1 + (c >> 1)) << (s + 1)) + 2 * a2 + (c & 1);
+}
+// coordinate d (0, 1) of the centre of space box a at level s
+__device__ __forceinline__ double sctr(int s, int64_t a, int d) {
+    const int64_t ad = d == 0 ? (a >> s) : (a & ((int64_t(1) << s) - 1));
+    return ldexp(double(ad) + 0.5, -s);
+}
+__device__ __forceinline__ double snode(const Cheb5& ch, int s, int64_t a, int d, int k) {
+    return sctr(s, a, d) + ldexp(0.5, -s) * ch.t[k];
+}
+__device__ __forceinline__ double fctr(int n, int l, int64_t b, int d) {
+    const int64_t bd = d == 0 ? (b >> l) : (b & ((int64_t(1) << l) - 1));
+    return -0.5 * n + (double(bd) + 0.5) * ldexp(double(n), -l);
+}
+__device__ __forceinline__ double fnode(const Cheb5& ch, int n, int l, int64_t b, int d, int k) {
+    return fctr(n, l, b, d) + ldexp(double(n), -l - 1) * ch.t[k];
+}
+
+// Morton position of the frequency (j1, j2): bits of j2 at even, of j1 at odd positions.
+__device__ __forceinline__ int64_t morton(int j1, int j2, int L) {
+    int64_t m = 0;
+    for (int k = 0; k < L; ++k) m |= (int64_t((j2 >> k) & 1) << (2 * k)) | (int64_t((j1 >> k) & 1) << (2 * k + 1));
+    return m;
+}
+__device__ __forceinline__ int64_t fidx(int j1, int j2, int n, int L, bool mort) {
+    return mort ? morton(j1, j2, L) : int64_t(j1) * n + j2;
+}
+
+// ---------------------------------------------------------------- tables
+__global__ void k2_tab_VP(float2* VP, int kind, int n, int sV) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= (int64_t(1) << (2 * sV)) * N) return;
+    const int64_t a = e / N, j = e % N;
+    VP[e] = expi(phi2(kind, sctr(sV, a, 0), sctr(sV, a, 1), double(j / n) - 0.5 * n, double(j % n) - 0.5 * n));
+}
+
+// groups g = tau 4^(L-s-1) + sigma', entries [g][o][c][t]
+__global__ void k2_tab_F(float2* F, int kind, Cheb5 ch, int n, int L, int s) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= N / 4 * 16 * R) return;
+    const int t = int(e % R);
+    const int64_t rest = e / R;
+    const int c = int(rest & 3), o = int((rest >> 2) & 3);
+    const int64_t g = rest >> 4;
+    const int64_t nbq = int64_t(1) << (2 * (L - s - 1));
+    const int64_t tau = g / nbq, sq = g % nbq;
+    const int64_t to = child_id(s, tau, o), beta = child_id(L - s - 1, sq, c);
+    const double g1 = fnode(ch, n, L - s, beta, 0, t / R1), g2 = fnode(ch, n, L - s, beta, 1, t % R1);
+    F[e] = expi(phi2(kind, sctr(s + 1, to, 0), sctr(s + 1, to, 1), g1, g2) -
+                phi2(kind, sctr(s, tau, 0), sctr(s, tau, 1), g1, g2));
+}
+
+__global__ void k2_tab_M(float2* M, int kind, Cheb5 ch, int n, int L, int h) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= N * R * R) return;
+    const int j = int(e % R), i = int((e / R) % R);
+    const int64_t p = e / (R * R);
+    const int64_t nb = int64_t(1) << (2 * (L - h));
+    const int64_t tau = p / nb, sg = p % nb;
+    const double z1 = snode(ch, h, tau, 0, i / R1), z2 = snode(ch, h, tau, 1, i % R1);
+    const double y1 = sctr(h, tau, 0), y2 = sctr(h, tau, 1);
+    const double g1 = fnode(ch, n, L - h, sg, 0, j / R1), g2 = fnode(ch, n, L - h, sg, 1, j % R1);
+    const double e1 = fctr(n, L - h, sg, 0), e2 = fctr(n, L - h, sg, 1);
+    M[e] = expi(phi2(kind, z1, z2, g1, g2) - phi2(kind, z1, z2, e1, e2) - phi2(kind, y1, y2, g1, g2));
+}
+
+__global__ void k2_tab_E(float2* E, int kind, Cheb5 ch, int n, int L, int s) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= N / 4 * 16 * R) return;
+    const int i = int(e % R);
+    const int64_t rest = e / R;
+    const int c = int(rest & 3), o = int((rest >> 2) & 3);
+    const int64_t g = rest >> 4;
+    const int64_t nbq = int64_t(1) << (2 * (L - s - 1));
+    const int64_t al = g / nbq, sq = g % nbq;
+    const int64_t to = child_id(s, al, o), beta = child_id(L - s - 1, sq, c);
+    const double z1 = snode(ch, s + 1, to, 0, i / R1), z2 = snode(ch, s + 1, to, 1, i % R1);
+    E[e] = expi(phi2(kind, z1, z2, fctr(n, L - s, beta, 0), fctr(n, L - s, beta, 1)) -
+                phi2(kind, z1, z2, fctr(n, L - s - 1, sq, 0), fctr(n, L - s - 1, sq, 1)));
+}
+
+__global__ void k2_tab_UP(float2* UP, int kind, int n, int L, int sU) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t nsg = int64_t(1) << (2 * (L - sU));
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= N * nsg) return;
+    const int64_t x = e / nsg, sg = e % nsg;
+    UP[e] = expi(phi2(kind, double(x / n) / n, double(x % n) / n, fctr(n, L - sU, sg, 0), fctr(n, L - sU, sg, 1)));
+}
+
+// ---------------------------------------------------------------- apply
+// Column block: X, Y (N x kc, ld); coefficient states S[col][pair][t] with
+// SN = N * 25 complex per column.
+
+// 25-term real-by-complex dot product of a padded smem row with a register vector.
+__device__ __forceinline__ float2 rowdot(const float* __restrict__ row, const float2 (&x)[R]) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 a = r4[q];
+        acc.x = fmaf(a.x, x[4 * q].x, acc.x); acc.y = fmaf(a.x, x[4 * q].y, acc.y);
+        acc.x = fmaf(a.y, x[4 * q + 1].x, acc.x); acc.y = fmaf(a.y, x[4 * q + 1].y, acc.y);
+        acc.x = fmaf(a.z, x[4 * q + 2].x, acc.x); acc.y = fmaf(a.z, x[4 * q + 2].y, acc.y);
+        acc.x = fmaf(a.w, x[4 * q + 3].x, acc.x); acc.y = fmaf(a.w, x[4 * q + 3].y, acc.y);
+    }
+    const float a24 = row[24];
+    acc.x = fmaf(a24, x[24].x, acc.x); acc.y = fmaf(a24, x[24].y, acc.y);
+    return acc;
+}
+
+// V (forward): c(a, b, t) = sum_q QV[t][q] VP[a][xi(b, q)] f(xi(b, q)).
+// CTA: one frequency leaf b, 4 columns; thread (a, column).
+__global__ void __launch_bounds__(TB) k2_V_fwd(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S,
+                                               int64_t SN, const float2* __restrict__ VP, const float* __restrict__ QV,
+                                               int n, int L, int sV, int kc, int mort) {
+    __shared__ float2 vps[64][65];
+    __shared__ float2 fs[4][64];
+    __shared__ float qv[R][64];
+    const int NA = 1 << (2 * sV), m = 1 << sV, lb = L - sV;
+    const int64_t N = int64_t(n) * n, NB = int64_t(1) << (2 * lb);
+    const int64_t b = blockIdx.x;
+    const int col0 = blockIdx.y * 4;
+    const int b1 = int(b >> lb), b2 = int(b & ((int64_t(1) << lb) - 1));
+    for (int idx = threadIdx.x; idx < NA * NA; idx += TB) {
+        const int a = idx / NA, q = idx % NA;
+        vps[a][q] = VP[a * N + int64_t(b1 * m + q / m) * n + b2 * m + q % m];
+    }
+    for (int idx = threadIdx.x; idx < 4 * NA; idx += TB) {
+        const int cl = idx / NA, q = idx % NA;
+        if (col0 + cl < kc) fs[cl][q] = X[(col0 + cl) * ld + fidx(b1 * m + q / m, b2 * m + q % m, n, L, mort)];
+    }
+    for (int idx = threadIdx.x; idx < R * NA; idx += TB) qv[idx / NA][idx % NA] = QV[idx];
+    __syncthreads();
+    const int a = threadIdx.x & 63, cl = threadIdx.x >> 6;
+    if (a >= NA || col0 + cl >= kc) return;
+    float2 acc[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int q = 0; q < NA; ++q) {
+        const float2 v = cmul(vps[a][q], fs[cl][q]);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            acc[t].x = fmaf(qv[t][q], v.x, acc[t].x);
+            acc[t].y = fmaf(qv[t][q], v.y, acc[t].y);
+        }
+    }
+    float2* out = S + (col0 + cl) * SN + (a * NB + b) * R;
+#pragma unroll
+    for (int t = 0; t < R; ++t) out[t] = acc[t];
+}
+
+// V^*: f(xi(b, q)) = sum_a conj(VP[a][xi]) sum_t QV[t][q] c(a, b, t).  Thread (q, column).
+__global__ void __launch_bounds__(TB) k2_V_adj(const float2* __restrict__ S, int64_t SN, float2* __restrict__ Y,
+                                               int64_t ld, const float2* __restrict__ VP, const float* __restrict__ QV,
+                                               int n, int L, int sV, int kc, int mort) {
+    extern __shared__ float4 smem_v[];
+    float2(*vps)[65] = reinterpret_cast<float2(*)[65]>(smem_v);                 // [64][65]
+    float2* cs = reinterpret_cast<float2*>(smem_v) + 64 * 65;                     // [4][64][R]
+    float* qv = reinterpret_cast<float*>(cs + 4 * 64 * R);                        // [R][64]
+    const int NA = 1 << (2 * sV), m = 1 << sV, lb = L - sV;
+    const int64_t N = int64_t(n) * n, NB = int64_t(1) << (2 * lb);
+    const int64_t b = blockIdx.x;
+    const int col0 = blockIdx.y * 4;
+    const int b1 = int(b >> lb), b2 = int(b & ((int64_t(1) << lb) - 1));
+    for (int idx = threadIdx.x; idx < NA * NA; idx += TB) {
+        const int a = idx / NA, q = idx % NA;
+        vps[a][q] = VP[a * N + int64_t(b1 * m + q / m) * n + b2 * m + q % m];
+    }
+    for (int idx = threadIdx.x; idx < 4 * NA * R; idx += TB) {
+        const int cl = idx / (NA * R), rem = idx % (NA * R), a = rem / R, t = rem % R;
+        if (col0 + cl < kc) cs[(cl * 64 + a) * R + t] = S[(col0 + cl) * SN + (a * NB + b) * R + t];
+    }
+    for (int idx = threadIdx.x; idx < R * NA; idx += TB) qv[(idx / NA) * 64 + idx % NA] = QV[idx];
+    __syncthreads();
+    const int q = threadIdx.x & 63, cl = threadIdx.x >> 6;
+    if (q >= NA || col0 + cl >= kc) return;
+    float qq[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) qq[t] = qv[t * 64 + q];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int a = 0; a < NA; ++a) {
+        const float2* c = cs + (cl * 64 + a) * R;
+        float2 tmp = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            tmp.x = fmaf(qq[t], c[t].x, tmp.x);
+            tmp.y = fmaf(qq[t], c[t].y, tmp.y);
+        }
+        cfmac(acc, vps[a][q], tmp);
+    }
+    Y[(col0 + cl) * ld + fidx(b1 * m + q / m, b2 * m + q % m, n, L, mort)] = acc;
+}
+
+// One transfer level between pair levels s and s+1 (C: SM = true forward,
+// false adjoint; B: SM = false forward, true adjoint).  Group g couples the
+// level-s pairs low(c) = (tau, child c of sigma') and the level-(s+1) pairs
+// high(o) = (child o of tau, sigma').  Forward reads low (w = c) and writes
+// high (u = o); the adjoint reads high (w = o) and writes low (u = c).
+//   SM: out[u][v] = sum_w sum_t A_w[v][t] (Ph[u,w,t] x[w][t])          A = Pc
+//   MS: out[u][v] = sum_w Ph[u,w,v] sum_t A_u[v][t] x[w][t]            A = Pc^T
+// Ph[u,w,.] = table[g][o][c][.] (conjugated for the adjoint).
+// Thread (group, column, u); 64 (group, column) items per CTA.
+template <bool SM, bool ADJ>
+__global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin, float2* __restrict__ Sout, int64_t SN,
+                                                  const float2* __restrict__ Ph, const float* __restrict__ Am, int L,
+                                                  int s, int kc) {
+    __shared__ __align__(16) float A[4 * R * RP];
+    for (int i = threadIdx.x; i < 4 * R * RP; i += TB) A[i] = Am[i];
+    __syncthreads();
+    const int u = threadIdx.x & 3;
+    const int64_t item = int64_t(blockIdx.x) * (TB / 4) + (threadIdx.x >> 2);
+    const int64_t ngroups = int64_t(1) << (2 * L - 2);
+    if (item >= ngroups * kc) return;
+    const int col = int(item % kc);
+    const int64_t g = item / kc;
+    const int64_t nbq = int64_t(1) << (2 * (L - s - 1));
+    const int64_t tau = g / nbq, sq = g % nbq;
+    auto low = [&](int c) { return tau * (nbq * 4) + child_id(L - s - 1, sq, c); };
+    auto high = [&](int o) { return child_id(s, tau, o) * nbq + sq; };
+    const float2* xin = Sin + col * SN;
+    float2 acc[R];
+#pragma unroll
+    for (int v = 0; v < R; ++v) acc[v] = make_float2(0.f, 0.f);
+    for (int w = 0; w < 4; ++w) {
+        const float2* x = xin + (ADJ ? high(w) : low(w)) * R;
+        const int o = ADJ ? w : u, c = ADJ ? u : w;
+        const float2* ph = Ph + ((g * 4 + o) * 4 + c) * R;
+        float2 xv[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) xv[t] = __ldg(x + t);
+        if (SM) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) xv[t] = ADJ ? cmulc(__ldg(ph + t), xv[t]) : cmul(__ldg(ph + t), xv[t]);
+            const float* Aw = A + w * R * RP;
+#pragma unroll
+            for (int v = 0; v < R; ++v) acc[v] = cadd(acc[v], rowdot(Aw + v * RP, xv));
+        } else {
+            const float* Au = A + u * R * RP;
+#pragma unroll
+            for (int v = 0; v < R; ++v) {
+                const float2 tmp = rowdot(Au + v * RP, xv);
+                if (ADJ) cfmac(acc[v], __ldg(ph + v), tmp);
+                else cfma(acc[v], __ldg(ph + v), tmp);
+            }
+        }
+    }
+    float2* out = Sout + col * SN + (ADJ ? low(u) : high(u)) * R;
+#pragma unroll
+    for (int v = 0; v < R; ++v) out[v] = acc[v];
+}
+
+// Middle level: y[i] = sum_j M[p][i][j] x[j] (adjoint: x[j] = sum_i conj(M[p][i][j]) y[i]).
+// CTA: 16 pairs x 16 columns; thread (pair, column).
+template <bool ADJ>
+__global__ void __launch_bounds__(TB) k2_M(const float2* __restrict__ Sin, float2* __restrict__ Sout, int64_t SN,
+                                           const float2* __restrict__ M, int64_t npairs, int kc) {
+    extern __shared__ float4 smem_m[];
+    float2* Ms = reinterpret_cast<float2*>(smem_m);   // [16][R*R]
+    const int64_t p0 = int64_t(blockIdx.x) * 16;
+    const int np = int(std::min<int64_t>(16, npairs - p0));
+    const float4* src = reinterpret_cast<const float4*>(M + p0 * R * R);
+    float4* dst = reinterpret_cast<float4*>(Ms);
+    for (int i = threadIdx.x; i < np * R * R / 2; i += TB) dst[i] = src[i];   // R*R*16 B per pair: even count of float4
+    if (np * R * R % 2) Ms[np * R * R - 1] = M[(p0 + np) * R * R - 1];
+    __syncthreads();
+    const int pl = threadIdx.x >> 4, col = blockIdx.y * 16 + (threadIdx.x & 15);
+    if (pl >= np || col >= kc) return;
+    const float2* m = Ms + pl * R * R;
+    const float2* x = Sin + col * SN + (p0 + pl) * R;
+    float2 acc[R];
+#pragma unroll
+    for (int v = 0; v < R; ++v) acc[v] = make_float2(0.f, 0.f);
+    for (int w = 0; w < R; ++w) {
+        const float2 xw = __ldg(x + w);
+        if (ADJ) {
+#pragma unroll
+            for (int v = 0; v < R; ++v) cfmac(acc[v], m[w * R + v], xw);
+        } else {
+#pragma unroll
+            for (int v = 0; v < R; ++v) cfma(acc[v], m[v * R + w], xw);
+        }
+    }
+    float2* y = Sout + col * SN + (p0 + pl) * R;
+#pragma unroll
+    for (int v = 0; v < R; ++v) y[v] = acc[v];
+}
+
+// U (forward): y(x) = sum_b UP[x][b] sum_i QU[x_loc][i] d(tau, b, i).
+// CTA: one space leaf tau, 4 columns; thread (x_loc, column).
+__global__ void __launch_bounds__(TB) k2_U_fwd(const float2* __restrict__ S, int64_t SN, float2* __restrict__ Y,
+                                               int64_t ld, const float2* __restrict__ UP, const float* __restrict__ QU,
+                                               int n, int L, int sU, int kc) {
+    extern __shared__ float4 smem_u[];
+    float2(*ups)[65] = reinterpret_cast<float2(*)[65]>(smem_u);
+    float2* ds = reinterpret_cast<float2*>(smem_u) + 64 * 65;      // [4][64][R]
+    float* qu = reinterpret_cast<float*>(ds + 4 * 64 * R);          // [64][R]
+    const int NP = 1 << (2 * (L - sU)), m = 1 << (L - sU);          // points per leaf = frequency boxes
+    const int64_t tau = blockIdx.x;
+    const int col0 = blockIdx.y * 4;
+    const int t1 = int(tau >> sU), t2 = int(tau & ((int64_t(1) << sU) - 1));
+    auto gx = [&](int x) { return int64_t(t1 * m + x / m) * n + t2 * m + x % m; };
+    for (int idx = threadIdx.x; idx < NP * NP; idx += TB) ups[idx / NP][idx % NP] = UP[gx(idx / NP) * NP + idx % NP];
+    for (int idx = threadIdx.x; idx < 4 * NP * R; idx += TB) {
+        const int cl = idx / (NP * R), rem = idx % (NP * R);
+        if (col0 + cl < kc) ds[cl * 64 * R + rem] = S[(col0 + cl) * SN + tau * NP * R + rem];
+    }
+    for (int idx = threadIdx.x; idx < NP * R; idx += TB) qu[idx] = QU[idx];
+    __syncthreads();
+    const int x = threadIdx.x & 63, cl = threadIdx.x >> 6;
+    if (x >= NP || col0 + cl >= kc) return;
+    float qq[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) qq[i] = qu[x * R + i];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < NP; ++b) {
+        const float2* d = ds + (cl * 64 + b) * R;
+        float2 tmp = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            tmp.x = fmaf(qq[i], d[i].x, tmp.x);
+            tmp.y = fmaf(qq[i], d[i].y, tmp.y);
+        }
+        cfma(acc, ups[x][b], tmp);
+    }
+    Y[(col0 + cl) * ld + gx(x)] = acc;
+}
+
+// U^*: d(tau, b, i) = sum_x QU[x_loc][i] conj(UP[x][b]) g(x).  Thread (b, column).
+__global__ void __launch_bounds__(TB) k2_U_adj(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S,
+                                               int64_t SN, const float2* __restrict__ UP, const float* __restrict__ QU,
+                                               int n, int L, int sU, int kc) {
+    __shared__ float2 ups[64][65];
+    __shared__ float2 gs[4][64];
+    __shared__ float qu[64 * R];
+    const int NP = 1 << (2 * (L - sU)), m = 1 << (L - sU);
+    const int64_t tau = blockIdx.x;
+    const int col0 = blockIdx.y * 4;
+    const int t1 = int(tau >> sU), t2 = int(tau & ((int64_t(1) << sU) - 1));
+    auto gx = [&](int x) { return int64_t(t1 * m + x / m) * n + t2 * m + x % m; };
+    for (int idx = threadIdx.x; idx < NP * NP; idx += TB) ups[idx / NP][idx % NP] = UP[gx(idx / NP) * NP + idx % NP];
+    for (int idx = threadIdx.x; idx < 4 * NP; idx += TB) {
+        const int cl = idx / NP, x = idx % NP;
+        if (col0 + cl < kc) gs[cl][x] = X[(col0 + cl) * ld + gx(x)];
+    }
+    for (int idx = threadIdx.x; idx < NP * R; idx += TB) qu[idx] = QU[idx];
+    __syncthreads();
+    const int b = threadIdx.x & 63, cl = threadIdx.x >> 6;
+    if (b >= NP || col0 + cl >= kc) return;
+    float2 acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int x = 0; x < NP; ++x) {
+        const float2 v = cmulc(ups[x][b], gs[cl][x]);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            acc[i].x = fmaf(qu[x * R + i], v.x, acc[i].x);
+            acc[i].y = fmaf(qu[x * R + i], v.y, acc[i].y);
+        }
+    }
+    float2* out = S + (col0 + cl) * SN + (tau * NP + b) * R;
+#pragma unroll
+    for (int i = 0; i < R; ++i) out[i] = acc[i];
+}
+
+// Lexicographic <- Morton reordering of frequency vectors: X[j] = Xm[morton(j)].
+__global__ void k2_unmorton(const float2* __restrict__ Xm, float2* __restrict__ X, int n, int L, int64_t ld) {
+    const int64_t N = int64_t(n) * n;
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int col = blockIdx.y;
+    X[col * ld + j] = Xm[col * ld + morton(int(j / n), int(j % n), L)];
+}
+
+constexpr size_t kSmemVadj = (64 * 65 + 4 * 64 * R) * sizeof(float2) + R * 64 * sizeof(float);
+constexpr size_t kSmemUfwd = (64 * 65 + 4 * 64 * R) * sizeof(float2) + 64 * R * sizeof(float);
+constexpr size_t kSmemM = 16 * R * R * sizeof(float2);
+
+size_t off_P() { return 0; }
+size_t off_PT() { return size_t(4) * R * RP; }
+size_t off_QV() { return size_t(8) * R * RP; }
+size_t off_QU(int NA) { return off_QV() + size_t(R) * NA; }
+
+}  // namespace
+
+bool bf2d_ok_kind(int kind) { return kind == FIO_PHASE_DFT || kind == FIO_PHASE_2D_ELLIPTIC; }
+
+fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
+    const int n = bf->nside, L = bf->L, r1 = R1;
+    const int NA = 1 << (2 * bf->sV), NP = 1 << (2 * (L - bf->sU));
+    const int mV = 1 << bf->sV, mU = 1 << (L - bf->sU);
+    Cheb5 ch;
+    for (int k = 0; k < r1; ++k) ch.t[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * r1));
+    // real tables: Pc, Pc^T, QV, QU
+    std::vector<float> P(off_QU(NA) + size_t(NP) * R, 0.f);
+    auto l1 = [&](int k, double u) { return lagrange_host(ch.t, r1, k, u); };
+    for (int c = 0; c < 4; ++c)
+        for (int j = 0; j < R; ++j)
+            for (int t = 0; t < R; ++t) {
+                const double v = l1(j / r1, (c >> 1) - 0.5 + 0.5 * ch.t[t / r1]) * l1(j % r1, (c & 1) - 0.5 + 0.5 * ch.t[t % r1]);
+                P[off_P() + (c * R + j) * RP + t] = float(v);
+                P[off_PT() + (c * R + t) * RP + j] = float(v);
+            }
+    for (int t = 0; t < R; ++t)
+        for (int q = 0; q < NA; ++q)
+            P[off_QV() + t * NA + q] =
+                float(l1(t / r1, 2.0 * (q / mV) / mV - 1.0) * l1(t % r1, 2.0 * (q % mV) / mV - 1.0));
+    for (int x = 0; x < NP; ++x)
+        for (int i = 0; i < R; ++i)
+            P[off_QU(NA) + x * R + i] =
+                float(l1(i / r1, 2.0 * (x / mU) / mU - 1.0) * l1(i % r1, 2.0 * (x % mU) / mU - 1.0));
+    FIO_TRY(bf->P.ensure(P.size() * sizeof(float)));
+    FIO_CUDA(cudaMemcpyAsync(bf->P.p, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    const int64_t N = int64_t(n) * n;
+    const int kind = bf->phase.kind;
+    const int64_t nVP = int64_t(NA) * N, nUP = N * NP, nM = N * R * R, nT = N / 4 * 16 * R;
+    FIO_TRY(bf->VP.ensure(nVP * 8));
+    FIO_TRY(bf->UP.ensure(nUP * 8));
+    FIO_TRY(bf->M.ensure(nM * 8));
+    k2_tab_VP<<<cdiv(nVP, TB), TB, 0, st>>>(bf->VP.as<float2>(), kind, n, bf->sV);
+    k2_tab_UP<<<cdiv(nUP, TB), TB, 0, st>>>(bf->UP.as<float2>(), kind, n, L, bf->sU);
+    k2_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), kind, ch, n, L, bf->h);
+    bf->C.resize(bf->h - bf->sV);
+    for (int s = bf->sV; s < bf->h; ++s) {
+        FIO_TRY(bf->C[s - bf->sV].ensure(nT * 8));
+        k2_tab_F<<<cdiv(nT, TB), TB, 0, st>>>(bf->C[s - bf->sV].as<float2>(), kind, ch, n, L, s);
+    }
+    bf->B.resize(bf->sU - bf->h);
+    for (int s = bf->h; s < bf->sU; ++s) {
+        FIO_TRY(bf->B[s - bf->h].ensure(nT * 8));
+        k2_tab_E<<<cdiv(nT, TB), TB, 0, st>>>(bf->B[s - bf->h].as<float2>(), kind, ch, n, L, s);
+    }
+    FIO_CUDA(cudaGetLastError());
+    FIO_CUDA(cudaStreamSynchronize(st));
+    bf->table_bytes = (nVP + nUP + nM + nT * int64_t(bf->C.size() + bf->B.size())) * 8 + int64_t(P.size()) * 4;
+    static bool attrs = false;
+    if (!attrs) {
+        FIO_CUDA(cudaFuncSetAttribute(k2_V_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemVadj)));
+        FIO_CUDA(cudaFuncSetAttribute(k2_U_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemUfwd)));
+        FIO_CUDA(cudaFuncSetAttribute(k2_M<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM)));
+        FIO_CUDA(cudaFuncSetAttribute(k2_M<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM)));
+        attrs = true;
+    }
+    return FIO_OK;
+}
+
+// kc columns; states s0, s1 of N * 25 * kc complex each.
+fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool mort,
+                           float2* s0, float2* s1, cudaStream_t st) {
+    const int n = bf->nside, L = bf->L, h = bf->h, sU = bf->sU, sV = bf->sV;
+    const int64_t N = int64_t(n) * n, SN = N * R;
+    const int NA = 1 << (2 * sV);
+    const float* Pm = bf->P.as<float>();
+    const float* QV = Pm + off_QV();
+    const float* QU = Pm + off_QU(NA);
+    const int64_t ngroups = N / 4;
+    const unsigned gtr = cdiv(ngroups * kc, TB / 4);
+    const dim3 gV(unsigned(int64_t(1) << (2 * (L - sV))), cdiv(kc, 4));
+    const dim3 gU(unsigned(int64_t(1) << (2 * sU)), cdiv(kc, 4));
+    const dim3 gM(cdiv(N, 16), cdiv(kc, 16));
+    float2* cur = s0;
+    float2* oth = s1;
+    const int m = mort ? 1 : 0;
+    if (!adjoint) {
+        FIO_LAUNCH("k2_V_fwd", st, k2_V_fwd<<<gV, TB, 0, st>>>(X, ld, cur, SN, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
+        for (int s = sV; s < h; ++s) {
+            FIO_LAUNCH("k2_C_fwd", st, (k2_trans<true, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+                                                                                 Pm + off_P(), L, s, kc)));
+            std::swap(cur, oth);
+        }
+        FIO_LAUNCH("k2_M_fwd", st, k2_M<false><<<gM, TB, kSmemM, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc));
+        std::swap(cur, oth);
+        for (int s = h; s < sU; ++s) {
+            FIO_LAUNCH("k2_B_fwd", st, (k2_trans<false, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+                                                                                  Pm + off_PT(), L, s, kc)));
+            std::swap(cur, oth);
+        }
+        FIO_LAUNCH("k2_U_fwd", st, k2_U_fwd<<<gU, TB, kSmemUfwd, st>>>(cur, SN, Y, ld, bf->UP.as<float2>(), QU, n, L, sU, kc));
+    } else {
+        FIO_LAUNCH("k2_U_adj", st, k2_U_adj<<<gU, TB, 0, st>>>(X, ld, cur, SN, bf->UP.as<float2>(), QU, n, L, sU, kc));
+        for (int s = sU - 1; s >= h; --s) {
+            FIO_LAUNCH("k2_B_adj", st, (k2_trans<true, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+                                                                                Pm + off_P(), L, s, kc)));
+            std::swap(cur, oth);
+        }
+        FIO_LAUNCH("k2_M_adj", st, k2_M<true><<<gM, TB, kSmemM, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc));
+        std::swap(cur, oth);
+        for (int s = h - 1; s >= sV; --s) {
+            FIO_LAUNCH("k2_C_adj", st, (k2_trans<false, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+                                                                                 Pm + off_PT(), L, s, kc)));
+            std::swap(cur, oth);
+        }
+        FIO_LAUNCH("k2_V_adj", st, k2_V_adj<<<gV, TB, kSmemVadj, st>>>(cur, SN, Y, ld, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+fio_status bf2d_unmorton(const fio_bf* bf, const float2* Xm, float2* X, int64_t ld, int k, cudaStream_t st) {
+    const int64_t N = int64_t(bf->nside) * bf->nside;
+    for (int c0 = 0; c0 < k; c0 += 65535) {
+        const int cc = std::min(65535, k - c0);
+        FIO_LAUNCH("k2_unmorton", st, (k2_unmorton<<<dim3(cdiv(N, TB), cc), TB, 0, st>>>(Xm + c0 * ld, X + c0 * ld,
+                                                                                        bf->nside, bf->L, ld)));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+}  // namespace fio

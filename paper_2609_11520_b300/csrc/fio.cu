@@ -36,13 +36,19 @@ extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, vo
     fio_hss* h = const_cast<fio_hss*>(hc);
     cudaStream_t st = as_stream(stream);
     const int64_t N = h->N;
+    // 2D: the HSS is over the frequency index in quadtree (Morton) order; the
+    // solve runs in that order and the result is reordered at the end.
+    const bool mort = bf->d == 2;
     // buffers: T (K~^* u in the handle's precision), R1, R2 (refinement), T32 (FP32 K~^* u
     // when the handle computes in split precision)
     const bool split_refine = refine_steps > 0 && bf->split;
-    const int nbuf = refine_steps > 0 ? (split_refine ? 4 : 3) : 1;
+    const int nbuf = (refine_steps > 0 ? (split_refine ? 4 : 3) : 1) + (mort ? 1 : 0);
     FIO_TRY(h->fio_ws.ensure(size_t(nbuf) * ld * k * 8));
     float2* T = h->fio_ws.as<float2>();
-    FIO_TRY(bf_apply(bf, U, T, ld, k, 1, st));                 // T = K~^* u
+    float2* Fout = static_cast<float2*>(F);
+    if (mort) F = T + size_t(nbuf - 1) * ld * k;               // solution in Morton order
+    const float2* Uc = static_cast<const float2*>(U);
+    FIO_TRY(bf_apply_ord(bf, Uc, T, ld, k, 1, mort, st));      // T = K~^* u
     FIO_TRY(hss_solve(h, T, F, ld, k, st));                    // f = G~^{-1} T
     if (refine_steps > 0) {
         float2* R1 = T + ld * k;
@@ -54,12 +60,12 @@ extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, vo
         fio_status s = FIO_OK;
         if (split_refine) {
             T32 = R2 + ld * k;
-            s = bf_apply(bf, U, T32, ld, k, 1, st);
+            s = bf_apply_ord(bf, Uc, T32, ld, k, 1, mort, st);
         }
         dim3 g(cdiv(N, 256), k);
         for (int it = 0; it < refine_steps && s == FIO_OK; ++it) {
-            s = bf_apply(bf, F, R1, ld, k, 0, st);                        // K~ f
-            if (s == FIO_OK) s = bf_apply(bf, R1, R2, ld, k, 1, st);      // K~^* K~ f
+            s = bf_apply_ord(bf, static_cast<const float2*>(F), R1, ld, k, 0, mort, st);   // K~ f
+            if (s == FIO_OK) s = bf_apply_ord(bf, R1, R2, ld, k, 1, mort, st);             // K~^* K~ f
             if (s != FIO_OK) break;
             FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T32, R2, R1, N, ld, ld, ld));
             s = hss_solve(h, R1, R2, ld, k, st);
@@ -68,6 +74,7 @@ extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, vo
         bf->split = was_split;
         FIO_TRY(s);
     }
+    if (mort) FIO_TRY(bf2d_unmorton(bf, static_cast<const float2*>(F), Fout, ld, k, st));
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
 }

@@ -478,9 +478,10 @@ namespace {
 // H X for the sampler, X and Z: N x s, ld = N.  T is scratch (N x s).
 fio_status sample(const fio_sampler* sm, int64_t N, const float2* X, float2* Z, float2* T, int s, cudaStream_t st) {
     if (sm->kind == FIO_SAMPLER_NORMAL) {
+        // 2D: the HSS is built over the frequency index in quadtree (Morton) order
         fio_bf* bf = const_cast<fio_bf*>(sm->bf);
-        FIO_TRY(bf_apply(bf, X, T, N, s, 0, st));
-        FIO_TRY(bf_apply(bf, T, Z, N, s, 1, st));
+        FIO_TRY(bf_apply_ord(bf, X, T, N, s, 0, true, st));
+        FIO_TRY(bf_apply_ord(bf, T, Z, N, s, 1, true, st));
         return FIO_OK;
     }
     dim3 g(cdiv(N, 16), cdiv(s, 16)), b(16, 16);
@@ -530,6 +531,17 @@ fio_status sample_level(fio_hss* h, const fio_sampler* sm, int l, const float2* 
     return FIO_OK;
 }
 
+// Opt a kernel into `bytes` of dynamic shared memory (above the 48 KB default).
+constexpr size_t kMaxDynSmem = 227 * 1024;
+template <class Kern>
+fio_status dyn_smem(Kern kernel, size_t bytes, const char* what) {
+    if (bytes > kMaxDynSmem)
+        return fail(FIO_EINVAL, std::string(what) + ": node needs " + std::to_string(bytes) +
+                                    " bytes of shared memory (227 KB per CTA); sample count or rank too large");
+    if (bytes > 48 * 1024) FIO_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    return FIO_OK;
+}
+
 template <class C>
 fio_status level_nodes(fio_hss* h, int l, int m, int s, int rhat, const float2* Om, const float2* Y, double tol,
                        DevBuf& ws, DevBuf& thr, DevBuf& khat, DevBuf& sat, DevBuf& taus, std::vector<int>& hk,
@@ -540,8 +552,10 @@ fio_status level_nodes(fio_hss* h, int l, int m, int s, int rhat, const float2* 
     FIO_TRY(khat.ensure(size_t(nn) * 4));
     FIO_TRY(sat.ensure(size_t(nn) * 4));
     FIO_TRY(taus.ensure(size_t(nn) * std::max(1, rhat) * sizeof(C)));
+    FIO_TRY(dyn_smem(k_node_lq<C>, size_t(s) * sizeof(C), "hss_build_from_samples"));
     k_node_lq<C><<<nn, TB, size_t(s) * sizeof(C), st>>>(Om, Y, h->rows(l), m, s, ws.as<C>(), thr.as<double>(), tol);
     size_t shq = (size_t((s - m + 1) & ~1)) * sizeof(typename RealOf<C>::T) + size_t(m) * sizeof(C);
+    FIO_TRY(dyn_smem(k_node_qrcp<C>, shq, "hss_build_from_samples"));
     k_node_qrcp<C><<<nn, TB, shq, st>>>(ws.as<C>(), m, s, rhat, thr.as<double>(), khat.as<int>(), sat.as<int>(),
                                        taus.as<C>());
     FIO_CUDA(cudaGetLastError());
@@ -675,6 +689,10 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
         h->samples += s0;
         if ((s = ws.ensure(size_t(2) * m0 * s0 * 16)) != FIO_OK) { release(); return bail(s); }
         if ((s = thr.ensure(16)) != FIO_OK) { release(); return bail(s); }
+        if ((s = dyn_smem(k_node_lq<double2>, size_t(s0) * 16, "hss_build_from_samples (root)")) != FIO_OK) {
+            release();
+            return bail(s);
+        }
         k_node_lq<double2><<<1, TB, size_t(s0) * 16, st>>>(Om.as<float2>(), Yb.as<float2>(), m0, m0, s0, ws.as<double2>(),
                                                          thr.as<double>(), tol);
         k_root_h0<double2><<<1, TB, 0, st>>>(ws.as<double2>(), m0, s0, Dcur.as<double2>());

@@ -64,6 +64,7 @@ extern "C" fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y,
     if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply_noalloc: need k >= 0 and ld >= N");
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply_noalloc: null vector");
+    if (bf->d != 1) return fail(FIO_EINVAL, "bf_apply_noalloc: 1D handles only (use bf_apply)");
     const int64_t stateN = int64_t(bf->n) * bf->r;   // one column of coefficient state
     const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || bf->split);
     const int nstate = fused ? 1 : 2;

@@ -1,0 +1,130 @@
+"""2D butterfly (quadtree, r = 25) and the 2D online solve against the oracle.
+
+Tolerances: FP32 bf_apply rel-l2 <= 1e-5 against the oracle's apply of the
+same factors; GPU solve error against f_true no worse than 2x the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+from fio_inputs import crandn
+from oracle.butterfly2d import Butterfly2D
+from oracle.problem import Phase
+from oracle.solver import FIOSolver2D
+from tests.gpu_util import rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("k", [1, 5, 37])
+def test_bf2d_apply_matches_oracle(n, k):
+    """n = 8..128 spans 0..1 transfer levels and leaves of 16..64 points; k = 37 is
+    ragged over the 32-column chunks and the 4-column leaf CTAs."""
+    from paper_2609_11520_b300 import BF
+    if n == 128 and k == 37:
+        k = 9
+    ob = Butterfly2D(Phase("elliptic2d"), n, 5)
+    gb = BF(n, 25, "elliptic2d")
+    f = crandn(n * n, k, seed=100 * n + k)
+    assert rel(to_np(gb.apply(to_dev(f))), ob.apply(f)) < TOL
+    assert rel(to_np(gb.adjoint(to_dev(f))), ob.adjoint(f)) < TOL
+
+
+def test_bf2d_full_size_vs_oracle():
+    """n = 256 (N = 2^16, one C and one B level): one column each way against the oracle."""
+    from paper_2609_11520_b300 import BF
+    n = 256
+    ob = Butterfly2D(Phase("elliptic2d"), n, 5)
+    gb = BF(n, 25, "elliptic2d")
+    f = crandn(n * n, 1, seed=11)
+    assert rel(to_np(gb.apply(to_dev(f))), ob.apply(f)) < TOL
+    g = crandn(n * n, 1, seed=12)
+    assert rel(to_np(gb.adjoint(to_dev(g))), ob.adjoint(g)) < TOL
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_bf2d_dft_is_kronecker_of_1d(n):
+    """Phi = x.xi separates: the 2D BF equals K~_1 (x) K~_1 of the 1D BF with r = 5 on the
+    same levels, i.e. K~_2 vec(F) = vec(K~_1 F K~_1^T) (row-major vec), at any size."""
+    from paper_2609_11520_b300 import BF
+    b2 = BF(n, 25, "dft", d=2)
+    b1 = BF(n, 5, "dft")
+    b1.set_path("per_level")
+    Fm = torch.from_numpy(crandn(n, n, seed=5).astype(np.complex64)).cuda()     # F[j1, j2]
+    y2 = b2.apply(Fm.reshape(1, n * n)).reshape(n, n)
+    a = b1.apply(Fm.T.contiguous())          # columns of F (fixed j2) -> K1 F[:, j2]; rows of a: j2
+    y1 = b1.apply(a.T.contiguous())          # then along j2 for each i1: rows i1
+    assert float(torch.linalg.norm(y2 - y1) / torch.linalg.norm(y1)) < 1e-5
+
+
+def test_bf2d_adjoint_identity_full_size():
+    from paper_2609_11520_b300 import BF
+    gb = BF(256, 25, "elliptic2d")
+    x = to_dev(crandn(256 * 256, 1, seed=1))
+    y = to_dev(crandn(256 * 256, 1, seed=2))
+    lhs = torch.vdot(y.flatten(), gb.apply(x).flatten())
+    rhs = torch.vdot(gb.adjoint(y).flatten(), x.flatten())
+    assert abs(complex(lhs - rhs)) / abs(complex(lhs)) < 1e-5
+
+
+def test_bf2d_rejections():
+    from paper_2609_11520_b300 import BF, Batch, FioError, HSS
+    with pytest.raises(FioError):
+        BF(64, 16, "elliptic2d")                     # 2D needs r = 25
+    with pytest.raises(FioError):
+        BF(4, 25, "elliptic2d")                      # n >= 8
+    with pytest.raises(FioError):
+        BF(64, 25, "cabs", d=2)                      # the cabs phase is 1D
+    b = BF(16, 25, "elliptic2d")
+    with pytest.raises(FioError):
+        b.set_path("fused")
+    with pytest.raises(FioError):
+        b.set_precision("split_bf16")
+    g = HSS.from_samples(bf=b, leaf=64, oversample=10, tol=1e-3, seed=1).factor()
+    with pytest.raises(FioError):
+        Batch([(b, g)])
+
+
+def test_solve2d_matches_oracle():
+    """n = 32 (N = 1024), leaf 64, tol 1e-3: same Philox test matrices on both sides; the GPU
+    solve error against f_true is within 2x the oracle's, and one refinement step helps."""
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    n, leaf, p, tol, seed = 32, 64, 10, 1e-3, 1
+    S = FIOSolver2D(Phase("elliptic2d"), n, 5, leaf, p, tol, seed)
+    f = crandn(n * n, 3, seed=0)
+    u = S.bf.apply(f)
+    e_oracle = rel(S.solve(u), f)
+    bf = BF(n, 25, "elliptic2d")
+    g = HSS.from_samples(bf=bf, leaf=leaf, oversample=p, tol=tol, seed=seed).factor()
+    U = to_dev(u)
+    e_gpu = rel(to_np(fio_solve(bf, g, U)), f)
+    assert e_gpu <= 2 * e_oracle, (e_gpu, e_oracle)
+    e_ref = rel(to_np(fio_solve(bf, g, U, refine_steps=1)), f)
+    assert e_ref < e_gpu
+    ranks = g.info()["ranks"]   # FP32 vs FP64 truncation may move a rank by a few
+    assert all(abs(a - b) <= max(4, b // 10) for a, b in zip(ranks[1:], S.hss.ranks[1:])), (ranks, S.hss.ranks)
+
+
+def test_hss2d_approximates_normal_operator():
+    """n = 64, leaf 256: G~ (Morton order) against K~^* K~ on random vectors, within ~tol."""
+    from paper_2609_11520_b300 import BF, HSS
+    n = 64
+    bf = BF(n, 25, "elliptic2d")
+    g = HSS.from_samples(bf=bf, leaf=256, oversample=10, tol=1e-3, seed=3)
+    from oracle.problem import morton_order
+    perm = torch.from_numpy(morton_order(n)).cuda()
+    X = to_dev(crandn(n * n, 4, seed=9))              # (4, N), Morton order
+    Xl = torch.empty_like(X)
+    Xl[:, perm] = X                                    # lexicographic
+    Yl = bf.adjoint(bf.apply(Xl))
+    ref = Yl[:, perm]
+    got = g.matvec(X)
+    assert float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref)) < 2e-2
