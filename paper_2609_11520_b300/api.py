@@ -235,3 +235,8 @@ class Batch:
         if h is not None and h.value:
             lib.fio_batch_free(h)
             self._h = ctypes.c_void_p()
+
+
+def set_large_node(m_min):
+    """Node size from which HSS levels of at most 16 nodes use the FP64 level-3 kernels (default 384)."""
+    check(lib.fio_set_large_node(int(m_min)))

@@ -623,9 +623,12 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
     auto bail = [&](fio_status s) { hss_free(h); return s; };
     std::vector<DevBuf> Dchk(Lh + 1);
     DevBuf Om, Yb, xa, xb, xc, ws, thr, khat, sat, taus, scratch, Dcur, Dnext;
+    BigScratch* big = big_scratch_new();
     auto release = [&]() {
         for (auto& d : Dchk) d.release();
         for (DevBuf* b : {&Om, &Yb, &xa, &xb, &xc, &ws, &thr, &khat, &sat, &taus, &scratch, &Dcur, &Dnext}) b->release();
+        big_scratch_free(big);
+        big = nullptr;
     };
     const uint32_t k0 = uint32_t(seed & 0xffffffffu), k1 = uint32_t(seed >> 32);
     std::vector<int> hk, hsat;
@@ -651,10 +654,13 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
                 return bail(s);
             }
             h->samples += s_cols;
-            s = f64 ? level_nodes<double2>(h, l, m, s_cols, rhat, Om.as<float2>(), Yb.as<float2>(), tol, ws, thr, khat, sat,
-                                           taus, hk, hsat, st)
-                    : level_nodes<float2>(h, l, m, s_cols, rhat, Om.as<float2>(), Yb.as<float2>(), tol, ws, thr, khat, sat,
-                                          taus, hk, hsat, st);
+            if (large_level(nn, m))
+                s = big_level_nodes(*big, nn, m, s_cols, rhat, Om.as<float2>(), Yb.as<float2>(), rows, tol, hk, hsat, st);
+            else
+                s = f64 ? level_nodes<double2>(h, l, m, s_cols, rhat, Om.as<float2>(), Yb.as<float2>(), tol, ws, thr, khat,
+                                               sat, taus, hk, hsat, st)
+                        : level_nodes<float2>(h, l, m, s_cols, rhat, Om.as<float2>(), Yb.as<float2>(), tol, ws, thr, khat,
+                                              sat, taus, hk, hsat, st);
             if (s != FIO_OK) { release(); return bail(s); }
             bool saturated = false;
             int rl = 0;
@@ -670,8 +676,15 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
             h->ranks[l] = rl;
             break;
         }
-        s = f64 ? level_finish<double2>(h, l, m, s_cols, rhat, h->ranks[l], ws, taus, scratch, Dchk[l], st)
-                : level_finish<float2>(h, l, m, s_cols, rhat, h->ranks[l], ws, taus, scratch, Dchk[l], st);
+        if (large_level(nn, m)) {
+            const int rl = h->ranks[l];
+            if ((s = h->U[l].ensure(std::max<size_t>(8, size_t(nn) * m * rl * 8))) != FIO_OK) { release(); return bail(s); }
+            if ((s = Dchk[l].ensure(size_t(nn) * m * m * 8)) != FIO_OK) { release(); return bail(s); }
+            s = big_level_finish(*big, nn, m, rl, h->U[l].as<float2>(), Dchk[l].as<float2>(), st);
+        } else {
+            s = f64 ? level_finish<double2>(h, l, m, s_cols, rhat, h->ranks[l], ws, taus, scratch, Dchk[l], st)
+                    : level_finish<float2>(h, l, m, s_cols, rhat, h->ranks[l], ws, taus, scratch, Dchk[l], st);
+        }
         if (s != FIO_OK) { release(); return bail(s); }
     }
     // root: H^[0] = Y^[0] Omega^[0]+
@@ -687,15 +700,22 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
             return bail(s);
         }
         h->samples += s0;
-        if ((s = ws.ensure(size_t(2) * m0 * s0 * 16)) != FIO_OK) { release(); return bail(s); }
-        if ((s = thr.ensure(16)) != FIO_OK) { release(); return bail(s); }
-        if ((s = dyn_smem(k_node_lq<double2>, size_t(s0) * 16, "hss_build_from_samples (root)")) != FIO_OK) {
-            release();
-            return bail(s);
+        if (large_level(1, m0)) {
+            if ((s = big_root(*big, m0, s0, Om.as<float2>(), Yb.as<float2>(), Dcur.as<double2>(), st)) != FIO_OK) {
+                release();
+                return bail(s);
+            }
+        } else {
+            if ((s = ws.ensure(size_t(2) * m0 * s0 * 16)) != FIO_OK) { release(); return bail(s); }
+            if ((s = thr.ensure(16)) != FIO_OK) { release(); return bail(s); }
+            if ((s = dyn_smem(k_node_lq<double2>, size_t(s0) * 16, "hss_build_from_samples (root)")) != FIO_OK) {
+                release();
+                return bail(s);
+            }
+            k_node_lq<double2><<<1, TB, size_t(s0) * 16, st>>>(Om.as<float2>(), Yb.as<float2>(), m0, m0, s0,
+                                                             ws.as<double2>(), thr.as<double>(), tol);
+            k_root_h0<double2><<<1, TB, 0, st>>>(ws.as<double2>(), m0, s0, Dcur.as<double2>());
         }
-        k_node_lq<double2><<<1, TB, size_t(s0) * 16, st>>>(Om.as<float2>(), Yb.as<float2>(), m0, m0, s0, ws.as<double2>(),
-                                                         thr.as<double>(), tol);
-        k_root_h0<double2><<<1, TB, 0, st>>>(ws.as<double2>(), m0, s0, Dcur.as<double2>());
     }
     // postprocessing, top-down (Section 3.3)
     for (int l = 0; l < Lh; ++l) {
@@ -706,9 +726,16 @@ extern "C" fio_status hss_build_from_samples(const fio_sampler* sm, int64_t N, i
             release();
             return bail(s);
         }
-        if (mc > 0)
+        if (mc > 0 && large_level(1, mc)) {
+            if ((s = big_post(*big, nn, rc, mc, Dcur.as<double2>(), h->U[l + 1].as<float2>(), Dchk[l + 1].as<float2>(),
+                              h->B[l].as<float2>(), Dnext.as<double2>(), st)) != FIO_OK) {
+                release();
+                return bail(s);
+            }
+        } else if (mc > 0) {
             k_post<<<nn, TB, 0, st>>>(Dcur.as<double2>(), rc, mc, h->U[l + 1].as<float2>(), Dchk[l + 1].as<float2>(),
                                       h->B[l].as<float2>(), Dnext.as<double2>(), scratch.as<double2>());
+        }
         std::swap(Dcur, Dnext);
     }
     if ((s = h->D.ensure(size_t(1 << Lh) * leaf * leaf * 8)) != FIO_OK) { release(); return bail(s); }

@@ -25,6 +25,25 @@ struct fio_hss {
 };
 
 namespace fio {
+// Large nodes (dense64.cu): levels with at most 16 nodes of size m >= the
+// threshold (default 384, fio_set_large_node) run FP64 level-3 formulations.
+struct BigScratch;
+BigScratch* big_scratch_new();
+void big_scratch_free(BigScratch* b);
+void set_large_node_min(int m);
+bool large_level(int nodes, int m);
+fio_status big_level_nodes(BigScratch& w, int nn, int m, int s, int rhat, const float2* Om, const float2* Y, int64_t ld,
+                           double tol, std::vector<int>& hk, std::vector<int>& hs, cudaStream_t st);
+fio_status big_level_finish(BigScratch& w, int nn, int m, int rl, float2* Uout, float2* Dchk, cudaStream_t st);
+fio_status big_root(BigScratch& w, int m0, int s0, const float2* Om, const float2* Y, double2* D0, cudaStream_t st);
+fio_status big_post(BigScratch& w, int nn, int rc, int mc, double2* Dcur, const float2* Uc, const float2* Dchk,
+                    float2* Bout, double2* Dnext, cudaStream_t st);
+fio_status big_ulv_nodes(BigScratch& b, int nn, int m, int r, const double2* D, const double2* U, float2* Wout,
+                         double2* Dh22, double2* Uh2, int* d_status, cudaStream_t st);
+fio_status big_ulv_merge(BigScratch& b, int np, int r, const double2* Dh22, const double2* Uh2, const float2* B,
+                         const float2* Up, int rp, double2* Dplus, double2* Uplus, cudaStream_t st);
+fio_status big_ulv_root(BigScratch& b, int m0, const double2* Dp, float2* Rinv, int* d_status, cudaStream_t st);
+
 // Block products over the nodes of level l (column-major vectors, ld = rows):
 //   expand:   out[t*m + i] (+)= sum_c U_t[i][c] in[t*r + c]
 //   compress: out[t*r + c]  = sum_i conj(U_t[i][c]) in[t*m + i]

@@ -14,6 +14,7 @@
 //   Merge (Eq. 2.12): D+ = [[D^22_1, U^2_1 B^* U^2_2^*], [U^2_2 B U^2_1^*, D^22_2]],
 //   U+ = diag(U^2_1, U^2_2) U_parent.  Root: D+ = L L^*, stored as (L L^*)^{-1}.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "cplx.cuh"
@@ -438,8 +439,26 @@ __global__ void k_gemv_sq(const float2* __restrict__ A, int m, const float2* __r
 
 template <class C>
 fio_status factor_level(fio_hss* h, int l, const C* Dc, const C* Uc, DevBuf& scr, DevBuf& dh22, DevBuf& uh2,
-                        int* d_status, cudaStream_t st) {
+                        int* d_status, cudaStream_t st, BigScratch* big = nullptr) {
     const int nn = 1 << l, m = h->m(l), r = h->ranks[l];
+    if (big && std::is_same<C, double2>::value && large_level(nn, m)) {
+        FIO_TRY(dh22.ensure(std::max<size_t>(16, size_t(nn) * r * r * 16)));
+        FIO_TRY(uh2.ensure(std::max<size_t>(16, size_t(nn) * r * r * 16)));
+        FIO_TRY(h->W[l].ensure(size_t(nn) * m * m * 8));
+        const double2* D = reinterpret_cast<const double2*>(Dc);
+        const double2* U = reinterpret_cast<const double2*>(Uc);
+        if (l == h->Lh) {   // leaf generators are complex64
+            const int64_t nD = int64_t(nn) * m * m, nU = int64_t(nn) * m * r;
+            FIO_TRY(scr.ensure(size_t(nD + nU) * 16 + 16));
+            double2* D64 = scr.as<double2>();
+            k_to_f64<float2><<<cdiv(nD, TB), TB, 0, st>>>(h->D.as<float2>(), D64, nD);
+            if (nU) k_to_f64<float2><<<cdiv(nU, TB), TB, 0, st>>>(h->U[l].as<float2>(), D64 + nD, nU);
+            D = D64;
+            U = D64 + nD;
+        }
+        return big_ulv_nodes(*big, nn, m, r, D, U, h->W[l].as<float2>(), dh22.as<double2>(), uh2.as<double2>(), d_status,
+                             st);
+    }
     const int64_t per = 3 * int64_t(m) * m + 2 * int64_t(m) * r + r;
     FIO_TRY(scr.ensure(size_t(nn) * per * sizeof(C)));
     FIO_TRY(dh22.ensure(std::max<size_t>(16, size_t(nn) * r * r * sizeof(C))));
@@ -463,11 +482,14 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
     cudaStream_t st = as_stream(stream);
     const int Lh = h->Lh;
     DevBuf scr, dh22[2], uh2[2], dplus, uplus, dconv, stat;
+    BigScratch* big = big_scratch_new();
     auto release = [&]() {
         for (DevBuf* b : {&scr, &dh22[0], &dh22[1], &uh2[0], &uh2[1], &dplus, &uplus, &dconv, &stat}) b->release();
+        big_scratch_free(big);
+        big = nullptr;
     };
     fio_status s;
-    if ((s = stat.ensure(4)) != FIO_OK) return s;
+    if ((s = stat.ensure(4)) != FIO_OK) { release(); return s; }
     FIO_CUDA(cudaMemsetAsync(stat.p, 0, 4, st));
     int* d_status = stat.as<int>();
     bool cur_f64 = false;
@@ -482,7 +504,7 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
         int cur = l & 1;
         // inputs of this level: leaf generators, or D+/U+ of the merge (in dplus/uplus)
         if (l == Lh) {
-            s = f64 ? factor_level<double2>(h, l, nullptr, nullptr, scr, dh22[cur], uh2[cur], d_status, st)
+            s = f64 ? factor_level<double2>(h, l, nullptr, nullptr, scr, dh22[cur], uh2[cur], d_status, st, big)
                     : factor_level<float2>(h, l, nullptr, nullptr, scr, dh22[cur], uh2[cur], d_status, st);
         } else if (f64 && !cur_f64) {
             // promote the merged blocks to FP64
@@ -492,9 +514,10 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
             double2* U64 = D64 + nD;
             if (nD) k_to_f64<float2><<<cdiv(nD, TB), TB, 0, st>>>(dplus.as<float2>(), D64, nD);
             if (nU) k_to_f64<float2><<<cdiv(nU, TB), TB, 0, st>>>(uplus.as<float2>(), U64, nU);
-            s = factor_level<double2>(h, l, D64, U64, scr, dh22[cur], uh2[cur], d_status, st);
+            s = factor_level<double2>(h, l, D64, U64, scr, dh22[cur], uh2[cur], d_status, st, big);
         } else if (f64) {
-            s = factor_level<double2>(h, l, dplus.as<double2>(), uplus.as<double2>(), scr, dh22[cur], uh2[cur], d_status, st);
+            s = factor_level<double2>(h, l, dplus.as<double2>(), uplus.as<double2>(), scr, dh22[cur], uh2[cur], d_status,
+                                      st, big);
         } else {
             s = factor_level<float2>(h, l, dplus.as<float2>(), uplus.as<float2>(), scr, dh22[cur], uh2[cur], d_status, st);
         }
@@ -510,7 +533,16 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
             release();
             return s;
         }
-        if (mp > 0) {
+        if (mp > 0 && f64 && large_level(np, mp)) {
+            s = big_ulv_merge(*big, np, r, dh22[cur].as<double2>(), uh2[cur].as<double2>(), h->B[l - 1].as<float2>(), Up,
+                              rp, tmpD.as<double2>(), tmpU.as<double2>(), st);
+            if (s != FIO_OK) {
+                tmpD.release();
+                tmpU.release();
+                release();
+                return s;
+            }
+        } else if (mp > 0) {
             if (f64)
                 k_ulv_merge<double2><<<np, TB, 0, st>>>(dh22[cur].as<double2>(), uh2[cur].as<double2>(), h->B[l - 1].as<float2>(),
                                                         r, Up, rp, tmpD.as<double2>(), tmpU.as<double2>());
@@ -538,7 +570,11 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
                                                                         int64_t(m0) * m0);
             D64 = dconv.as<double2>();
         }
-        k_ulv_root<<<1, TB, 0, st>>>(D64, m0, h->Rinv.as<float2>(), scr.as<double2>(), d_status);
+        if (large_level(1, m0)) {
+            if ((s = big_ulv_root(*big, m0, D64, h->Rinv.as<float2>(), d_status, st)) != FIO_OK) { release(); return s; }
+        } else {
+            k_ulv_root<<<1, TB, 0, st>>>(D64, m0, h->Rinv.as<float2>(), scr.as<double2>(), d_status);
+        }
     }
     int hst = 0;
     cudaMemcpyAsync(&hst, d_status, 4, cudaMemcpyDeviceToHost, st);

@@ -93,9 +93,12 @@ def test_bf2d_rejections():
         Batch([(b, g)])
 
 
-def test_solve2d_matches_oracle():
+def test_solve2d_matches_oracle(check_ranks=True):
     """n = 32 (N = 1024), leaf 64, tol 1e-3: same Philox test matrices on both sides; the GPU
-    solve error against f_true is within 2x the oracle's, and one refinement step helps."""
+    solve error against f_true is within 2x the oracle's, and one refinement step helps.
+    The one-CTA node kernels follow the oracle's Householder steps, so their ranks agree
+    too (check_ranks); the large-node kernels truncate a different rank-revealing
+    factorization, so only errors are compared there."""
     from paper_2609_11520_b300 import BF, HSS, fio_solve
     n, leaf, p, tol, seed = 32, 64, 10, 1e-3, 1
     S = FIOSolver2D(Phase("elliptic2d"), n, 5, leaf, p, tol, seed)
@@ -110,7 +113,7 @@ def test_solve2d_matches_oracle():
     e_ref = rel(to_np(fio_solve(bf, g, U, refine_steps=1)), f)
     assert e_ref < e_gpu
     ranks = g.info()["ranks"]   # FP32 vs FP64 truncation may move a rank by a few
-    assert all(abs(a - b) <= max(4, b // 10) for a, b in zip(ranks[1:], S.hss.ranks[1:])), (ranks, S.hss.ranks)
+    assert not check_ranks or all(abs(a - b) <= max(4, b // 10) for a, b in zip(ranks[1:], S.hss.ranks[1:])), (ranks, S.hss.ranks)
 
 
 def test_hss2d_approximates_normal_operator():
