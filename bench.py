@@ -247,6 +247,115 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def kernel2d_bytes(name, N, kc, sV, L, sU):
+    """Algorithmic HBM bytes of one 2D kernel launch (kc columns): coefficient states
+    N*25*kc complex64 in and out, the vectors, and each table read once."""
+    S = N * 25 * kc * 8
+    vec = N * kc * 8
+    if name.startswith("k2_V"):
+        return S + vec + (4 ** sV) * N * 8
+    if name.startswith("k2_U"):
+        return S + vec + N * (4 ** (L - sU)) * 8
+    if name.startswith("k2_C") or name.startswith("k2_B"):
+        return 2 * S + N * 4 * 25 * 8
+    if name.startswith("k2_M"):
+        return 2 * S + N * 625 * 8
+    return None
+
+
+def run_2d(args):
+    """2D workload: the K~^* apply of the quadtree BF at n = 256 (N = 2^16, r = 25) on
+    blocks of k = 16 RHS, and the full online solve at a smaller n (default 64) with its
+    offline stages timed."""
+    import torch
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    from paper_2609_11520_b300 import _lib
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, k = 256, 16
+    N = n * n
+    bf = BF(n, 25, "elliptic2d")
+    info = bf.info()
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy((rng.standard_normal((k, N)) + 1j * rng.standard_normal((k, N))).astype(np.complex64)).cuda()
+    Y = torch.empty_like(X)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    with Clocks(0) as clk:
+        adj = timed(lambda: bf.apply(X, adjoint=True, out=Y), args.steps, args.warmup)
+        fwd = timed(lambda: bf.apply(X, out=Y), args.steps, args.warmup)
+    _lib.lib.fio_profile_enable(1)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        bf.apply(X, adjoint=True, out=Y)
+    torch.cuda.synchronize()
+    buf = ctypes.create_string_buffer(1 << 16)
+    _lib.check(_lib.lib.fio_profile_report(buf, len(buf)))
+    _lib.lib.fio_profile_enable(0)
+    prof = parse_profile(buf.value.decode())
+    tot = sum(v[1] for v in prof.values())
+    peak, peak_src = load_peaks()
+    kernels = {}
+    for name, (cnt, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        nb = kernel2d_bytes(name, N, k, info["sV"], info["L"], info["sU"])
+        gbs = nb / (ms / cnt / 1e3) / 1e9 if nb else None
+        kernels[name] = {"launches": cnt, "ms_total": round(ms, 4), "share": round(ms / tot, 4),
+                         "bytes_per_launch": nb, "achieved_gbs": gbs}
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    tb = kernel2d_bytes(top[0], N, k, info["sV"], info["L"], info["sU"])
+    ach = tb / (top[1][1] / top[1][0] / 1e3) / 1e9
+    # full solve at a smaller n
+    ns = args.n2d
+    t0 = time.perf_counter()
+    bs = BF(ns, 25, "elliptic2d")
+    g = HSS.from_samples(bf=bs, leaf=256, oversample=10, tol=1e-3, seed=1)
+    t_hss = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.factor()
+    t_fac = time.perf_counter() - t0
+    f = crandn(ns * ns, k, seed=0)
+    Ft = torch.from_numpy(np.ascontiguousarray(f.T.astype(np.complex64))).cuda()
+    U = bs.apply(Ft)
+    OUT = torch.empty_like(U)
+    sol = timed(lambda: fio_solve(bs, g, U, out=OUT), args.steps, args.warmup)
+    e = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
+    fio_solve(bs, g, U, out=OUT, refine_steps=1)
+    e1 = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
+    line = {
+        "metric": "2D K~^* apply RHS/s (n = 256, N = 2^16, quadtree BF r = 25); 2D online solve", "unit": UNIT,
+        "value": k * args.steps / (sum(adj) / 1e3), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(adj), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "2d: Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), a = 1, n = 256, r = 25, k = 16 per apply",
+                   "l2": "flushed between timed steps (256 MiB write)", "table_bytes": info["table_bytes"]},
+        "forward": {"value": k * args.steps / (sum(fwd) / 1e3), "ms_per_step": statistics.mean(fwd)},
+        "kernels": kernels,
+        "roofline": {"kernel": top[0], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "peak_source": peak_src, "bytes_per_launch": tb, "traffic": None},
+        "solve": {"n": ns, "N": ns * ns, "leaf": 256, "tol": 1e-3, "k": k, "hss_build_s": round(t_hss, 2),
+                  "ulv_factor_s": round(t_fac, 2), "ranks": g.info()["ranks"], "rhs_per_s": k * args.steps / (sum(sol) / 1e3),
+                  "ms_per_solve": statistics.mean(sol), "e_direct_vs_f_true": e, "e_refine1": e1},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def run_batched(args):
     """Batched workload: 32 operators, N uniform over 2^12..2^17, 16 RHS each, one step = all 512 RHS."""
     import torch
@@ -353,7 +462,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=64)
-    ap.add_argument("--workload", default="large1d", choices=["large1d", "batched1d", "serving"])
+    ap.add_argument("--workload", default="large1d", choices=["large1d", "batched1d", "serving", "2d"])
+    ap.add_argument("--n2d", type=int, default=64)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -363,6 +473,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "2d":
+        return run_2d(args)
 
     import torch
     import torch.distributed as dist

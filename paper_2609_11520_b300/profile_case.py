@@ -10,6 +10,7 @@ captures only those launches.  Cases:
   bf_forward   Y = K~ X
   hss_solve    X = G~^{-1} B
   fio_solve    f = G~^{-1} K~^* u   (one online step)
+  bf2d_adjoint / bf2d_forward   the 2D quadtree BF (elliptic phase, r = 25), n per dimension
 --precision split_bf16 runs the BF applies on the split-precision kernels.
 Prints the mean CUDA-event time per repetition.
 """
@@ -27,7 +28,8 @@ from paper_2609_11520_b300 import BF, HSS, fio_solve  # noqa: E402
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="fio_solve", choices=["bf_adjoint", "bf_forward", "hss_solve", "fio_solve"])
+    ap.add_argument("--case", default="fio_solve",
+                    choices=["bf_adjoint", "bf_forward", "hss_solve", "fio_solve", "bf2d_adjoint", "bf2d_forward"])
     ap.add_argument("--n", type=int, default=1 << 16)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--r", type=int, default=16)
@@ -37,20 +39,22 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    bf = BF(args.n, args.r)
+    two_d = args.case.startswith("bf2d")
+    bf = BF(args.n, 25, "elliptic2d") if two_d else BF(args.n, args.r)
     hss = None
     if args.case in ("hss_solve", "fio_solve"):
         hss = HSS.from_samples(bf=bf, leaf=args.leaf, oversample=10, tol=args.tol, seed=2).factor()
-    bf.set_precision(args.precision)
+    if not two_d:
+        bf.set_precision(args.precision)
     rng = np.random.default_rng(0)
-    X = torch.from_numpy((rng.standard_normal((args.k, args.n)) + 1j * rng.standard_normal((args.k, args.n)))
+    X = torch.from_numpy((rng.standard_normal((args.k, bf.n)) + 1j * rng.standard_normal((args.k, bf.n)))
                          .astype(np.complex64)).cuda()
     Y = torch.empty_like(X)
 
     def run():
-        if args.case == "bf_adjoint":
+        if args.case in ("bf_adjoint", "bf2d_adjoint"):
             bf.apply(X, adjoint=True, out=Y)
-        elif args.case == "bf_forward":
+        elif args.case in ("bf_forward", "bf2d_forward"):
             bf.apply(X, out=Y)
         elif args.case == "hss_solve":
             hss.solve(X, out=Y)
