@@ -86,3 +86,21 @@ def test_pinned_outputs_and_pageable_inputs(ops):
             assert r.f is req[3]
         alone = fio_solve(bf, hss, req[2].cuda()).cpu()
         assert float(torch.linalg.norm(r.f - alone) / torch.linalg.norm(alone)) <= 1e-6
+
+
+def test_mixed_1d_2d_operators():
+    """A 2D operator (n = 32, N = 1024, quadtree BF, Morton-ordered HSS) served beside a 1D one:
+    every result equals the same request solved alone."""
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    from paper_2609_11520_b300.serve import Server
+    b1 = BF(4096, 16)
+    b2 = BF(32, 25, "elliptic2d")
+    ops = {"one_d": (b1, HSS.from_samples(bf=b1, leaf=128, oversample=10, tol=1e-3, seed=31).factor()),
+           "two_d": (b2, HSS.from_samples(bf=b2, leaf=64, oversample=10, tol=1e-3, seed=32).factor())}
+    reqs = make_trace(ops, 40, rate=4000.0, seed=4)
+    done = Server(ops, kmax=16, n_slots=2).run(reqs)
+    assert len(done) == len(reqs)
+    for r, (t, name, u) in zip(done, reqs):
+        bf, hss = ops[name]
+        alone = fio_solve(bf, hss, u.cuda()).cpu()
+        assert float(torch.linalg.norm(r.f - alone) / torch.linalg.norm(alone)) <= 1e-6
