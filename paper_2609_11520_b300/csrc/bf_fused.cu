@@ -34,6 +34,11 @@ constexpr int R = 16;
 // Pc[c] blocks in shared memory are PCS floats apart: the two blocks that the
 // lanes of a warp read together fall into different banks.
 constexpr int PCS = R * R + 4;
+// Leaf Lagrange tables in shared memory: rows of RS floats (lanes that read
+// different rows of one column hit different banks); at most kLeafMax rows
+// (8 points per leaf box, Section 5.2's practical top level).
+constexpr int RS = R + 1;
+constexpr int kLeafMax = 8;
 
 struct Tabs {
     const float2* t[24];
@@ -311,8 +316,14 @@ __global__ void __launch_bounds__(256, 2) k_bf_left(HalfArgs a) {
             const int leaf = xl / lsU, qq = xl - leaf * lsU;
             const int64_t xg = int64_t(box) * P + xl;
             const float2* Sc = S + col * P * R;
+            float2 up[kLeafMax];
+#pragma unroll
+            for (int b = 0; b < kLeafMax; ++b)
+                if (b < nbU) up[b] = __ldg(a.UP + xg * nbU + b);
             float2 out = make_float2(0.f, 0.f);
-            for (int b = 0; b < nbU; ++b) {
+#pragma unroll
+            for (int b = 0; b < kLeafMax; ++b) {
+                if (b >= nbU) break;
                 float2 d[R];
                 load_pair(Sc, leaf * nbU + b, d);
                 float2 acc = make_float2(0.f, 0.f);
@@ -322,7 +333,7 @@ __global__ void __launch_bounds__(256, 2) k_bf_left(HalfArgs a) {
                     acc.x = fmaf(pu, d[i].x, acc.x);
                     acc.y = fmaf(pu, d[i].y, acc.y);
                 }
-                cfma(out, __ldg(a.UP + xg * nbU + b), acc);
+                cfma(out, up[b], acc);
             }
             a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
         }
@@ -856,7 +867,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
         cp_commit();
     }
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
-    for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[e] = a.P[a.pu_off + e];
+    for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[(e / R) * RS + e % R] = a.P[a.pu_off + e];
     __syncthreads();
     // split-precision A fragments: forward B levels are mix-then-scale (P_o), adjoint B^* scale-then-mix (P_e^T)
     if (SPLIT) {
@@ -875,16 +886,21 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             const int leaf = lp / nbU, b = lp - leaf * nbU;
             const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsU;
             const float2* gv = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 mm[kLeafMax];   // all global loads of the leaf issued before the products
+#pragma unroll
+            for (int qq = 0; qq < kLeafMax; ++qq)
+                if (qq < lsU) mm[qq] = cmulc(__ldg(a.UP + (x0 + qq) * nbU + b), __ldg(gv + qq));
             float2 y[R];
 #pragma unroll
             for (int i = 0; i < R; ++i) y[i] = make_float2(0.f, 0.f);
-            for (int qq = 0; qq < lsU; ++qq) {
-                const float2 mm = cmulc(__ldg(a.UP + (x0 + qq) * nbU + b), gv[qq]);
+#pragma unroll
+            for (int qq = 0; qq < kLeafMax; ++qq) {
+                if (qq >= lsU) break;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    const float pu = sPU[qq * R + i];
-                    y[i].x = fmaf(pu, mm.x, y[i].x);
-                    y[i].y = fmaf(pu, mm.y, y[i].y);
+                    const float pu = sPU[qq * RS + i];
+                    y[i].x = fmaf(pu, mm[qq].x, y[i].x);
+                    y[i].y = fmaf(pu, mm[qq].y, y[i].y);
                 }
             }
             store_pair(S + col * P * R, lp, y);
@@ -912,18 +928,24 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             const int leaf = xl / lsU, qq = xl - leaf * lsU;
             const int64_t xg = int64_t(box) * P + xl;
             const float2* Sc = S + col * P * R;
+            float2 up[kLeafMax];
+#pragma unroll
+            for (int b = 0; b < kLeafMax; ++b)
+                if (b < nbU) up[b] = __ldg(a.UP + xg * nbU + b);
             float2 out = make_float2(0.f, 0.f);
-            for (int b = 0; b < nbU; ++b) {
+#pragma unroll
+            for (int b = 0; b < kLeafMax; ++b) {
+                if (b >= nbU) break;
                 float2 d[R];
                 load_pair(Sc, leaf * nbU + b, d);
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    const float pu = sPU[qq * R + i];
+                    const float pu = sPU[qq * RS + i];
                     acc.x = fmaf(pu, d[i].x, acc.x);
                     acc.y = fmaf(pu, d[i].y, acc.y);
                 }
-                cfma(out, __ldg(a.UP + xg * nbU + b), acc);
+                cfma(out, up[b], acc);
             }
             a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
         }
@@ -975,7 +997,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
         cp_commit();
     }
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
-    for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[e] = a.P[e];
+    for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[(e / R) * RS + e % R] = a.P[e];
     __syncthreads();
     // split-precision A fragments: adjoint C^* levels are mix-then-scale (P_o), forward C scale-then-mix (P_e^T)
     if (SPLIT) {
@@ -999,16 +1021,21 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             const int aa = lp / nl, leaf = lp - aa * nl;
             const int64_t x0 = int64_t(box) * P + int64_t(leaf) * lsV;
             const float2* f = a.X + int64_t(col0 + col) * a.ldx + x0;
+            float2 mm[kLeafMax];
+#pragma unroll
+            for (int qq = 0; qq < kLeafMax; ++qq)
+                if (qq < lsV) mm[qq] = cmul(__ldg(a.VP + int64_t(aa) * a.n + x0 + qq), __ldg(f + qq));
             float2 y[R];
 #pragma unroll
             for (int jj = 0; jj < R; ++jj) y[jj] = make_float2(0.f, 0.f);
-            for (int qq = 0; qq < lsV; ++qq) {
-                const float2 mm = cmul(__ldg(a.VP + int64_t(aa) * a.n + x0 + qq), f[qq]);
+#pragma unroll
+            for (int qq = 0; qq < kLeafMax; ++qq) {
+                if (qq >= lsV) break;
 #pragma unroll
                 for (int jj = 0; jj < R; ++jj) {
-                    const float pv = sPV[qq * R + jj];
-                    y[jj].x = fmaf(pv, mm.x, y[jj].x);
-                    y[jj].y = fmaf(pv, mm.y, y[jj].y);
+                    const float pv = sPV[qq * RS + jj];
+                    y[jj].x = fmaf(pv, mm[qq].x, y[jj].x);
+                    y[jj].y = fmaf(pv, mm[qq].y, y[jj].y);
                 }
             }
             store_pair(S + col * P * R, aa * nl + rev_bits(leaf, g.h - g.sV), y);
@@ -1023,18 +1050,24 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             const int64_t xg = int64_t(box) * P + xl;
             const float2* Sc = S + col * P * R;
             const int slotl = rev_bits(leaf, g.h - g.sV);
+            float2 vp[kLeafMax];
+#pragma unroll
+            for (int aa = 0; aa < kLeafMax; ++aa)
+                if (aa < na) vp[aa] = __ldg(a.VP + int64_t(aa) * a.n + xg);
             float2 out = make_float2(0.f, 0.f);
-            for (int aa = 0; aa < na; ++aa) {
+#pragma unroll
+            for (int aa = 0; aa < kLeafMax; ++aa) {
+                if (aa >= na) break;
                 float2 c[R];
                 load_pair(Sc, aa * nl + slotl, c);
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
-                    const float pv = sPV[qq * R + t];
+                    const float pv = sPV[qq * RS + t];
                     acc.x = fmaf(pv, c[t].x, acc.x);
                     acc.y = fmaf(pv, c[t].y, acc.y);
                 }
-                cfmac(out, __ldg(a.VP + int64_t(aa) * a.n + xg), acc);
+                cfmac(out, vp[aa], acc);
             }
             a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
         }
@@ -1070,9 +1103,9 @@ __global__ void __launch_bounds__(NT, 1) k_right3_group(const HalfArgs* __restri
 }
 
 inline size_t smem3(int P) {
-    return size_t(NT) * R * 8 + size_t(P <= 256 ? 2 : 1) * P * 256 + (2 * PCS + 8 * R) * sizeof(float);
+    return size_t(NT) * R * 8 + size_t(P <= 256 ? 2 : 1) * P * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float);
 }
-constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + 8 * R) * sizeof(float);
+constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float);
 
 template <bool SPLIT> void set_attrs3_t() {
     const int mx = int(kSmem3Max);
