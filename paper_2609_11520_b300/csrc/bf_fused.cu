@@ -750,13 +750,15 @@ __device__ void level3_tc(float2* S, const SplitFrag (&fa)[2], const float4* ph,
 // (pair of the chunk, column, output index), 16 lanes per (pair, column).
 template <bool LEFT>
 __device__ void mchunk3(float2* S, const float4* mb, int ck, const Geo& g) {
+    // 8 lanes per (pair, column), two outputs per lane: a quarter warp covers one
+    // pair, so its 16-byte M loads are consecutive and its state loads broadcast.
     const int P = g.P, CH = P / 8;
     const int nB = g.sU - g.h, lo = g.L - g.sU;
-    const int ntask = CH * g.KC * R;
+    const int ntask = CH * g.KC * (R / 2);
     for (int b0 = 0; b0 < ntask; b0 += NT) {
         const int id = b0 + threadIdx.x;
         const bool act = id < ntask;
-        const int jj = id & (R - 1), rest = id >> 4;
+        const int jq = id & 7, rest = id >> 3;
         const int pl = rest % CH, col = rest / CH;
         const int lp = ck * CH + pl;
         const int slot = LEFT ? ((rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB)) : lp;
@@ -765,21 +767,30 @@ __device__ void mchunk3(float2* S, const float4* mb, int ck, const Geo& g) {
         if (act) load_pair(Sc, slot, x);
         __syncwarp();
         if (act) {
-            const float2* mp = reinterpret_cast<const float2*>(mb + pl * R * 8);
-            float2 acc = make_float2(0.f, 0.f);
-            if (LEFT) {   // y_j = sum_i conj(M[i][j]) x_i, natural layout
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            if (LEFT) {   // y_j = sum_i conj(M[i][j]) x_i, natural layout; j = 2 jq, 2 jq + 1
+                const float4* mp = mb + pl * R * 8 + jq;
 #pragma unroll
-                for (int i = 0; i < R; ++i) cfmac(acc, mp[i * R + jj], x[i]);
-            } else {      // y_i = sum_j M[i][j] x_j, row i swizzled by (i & 7)
-                const float4* rowp = mb + (pl * R + jj) * 8;
+                for (int i = 0; i < R; ++i) {
+                    const float4 v = mp[i * 8];
+                    cfmac(a0, make_float2(v.x, v.y), x[i]);
+                    cfmac(a1, make_float2(v.z, v.w), x[i]);
+                }
+            } else {      // y_i = sum_j M[i][j] x_j, row i swizzled by (i & 7); i = 2 jq, 2 jq + 1
+                const float4* r0 = mb + (pl * R + 2 * jq) * 8;
+                const float4* r1 = r0 + 8;
+                const int s0 = (2 * jq) & 7, s1 = (2 * jq + 1) & 7;
 #pragma unroll
                 for (int m = 0; m < R / 2; ++m) {
-                    const float4 v = rowp[m ^ (jj & 7)];
-                    cfma(acc, make_float2(v.x, v.y), x[2 * m]);
-                    cfma(acc, make_float2(v.z, v.w), x[2 * m + 1]);
+                    const float4 v0 = r0[m ^ s0], v1 = r1[m ^ s1];
+                    cfma(a0, make_float2(v0.x, v0.y), x[2 * m]);
+                    cfma(a0, make_float2(v0.z, v0.w), x[2 * m + 1]);
+                    cfma(a1, make_float2(v1.x, v1.y), x[2 * m]);
+                    cfma(a1, make_float2(v1.z, v1.w), x[2 * m + 1]);
                 }
             }
-            Sc[sw(slot, jj)] = acc;
+            Sc[sw(slot, 2 * jq)] = a0;
+            Sc[sw(slot, 2 * jq + 1)] = a1;
         }
     }
 }
