@@ -39,6 +39,7 @@ constexpr int R1 = 5;
 constexpr int R = R1 * R1;      // 25
 constexpr int RP = 28;          // padded row of a real 25-vector (seven float4)
 constexpr int TB = 256;
+constexpr int kPhGroups = 8;    // transfer groups whose phase rows a CTA stages in shared memory
 
 struct Cheb5 {
     double t[R1];
@@ -277,11 +278,20 @@ __global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin
                                                   const float2* __restrict__ Ph, const float* __restrict__ Am, int L,
                                                   int s, int kc) {
     __shared__ __align__(16) float A[4 * R * RP];
+    __shared__ float2 phs[kPhGroups * 16 * R];   // phase rows of the CTA's groups (when they fit)
     for (int i = threadIdx.x; i < 4 * R * RP; i += TB) A[i] = Am[i];
+    const int64_t ngroups = int64_t(1) << (2 * L - 2);
+    const int64_t item0 = int64_t(blockIdx.x) * (TB / 4);
+    const int64_t g0 = item0 / kc;
+    const int ng = int(std::min<int64_t>(ngroups - 1, (item0 + TB / 4 - 1) / kc) - g0 + 1);
+    // MS reads one phase per output inside the product loop: stage them; SM reads its
+    // phases ahead of the products, where the global loads already overlap
+    const bool staged = !SM && ng <= kPhGroups;
+    if (staged)
+        for (int i = threadIdx.x; i < ng * 16 * R; i += TB) phs[i] = Ph[g0 * 16 * R + i];
     __syncthreads();
     const int u = threadIdx.x & 3;
-    const int64_t item = int64_t(blockIdx.x) * (TB / 4) + (threadIdx.x >> 2);
-    const int64_t ngroups = int64_t(1) << (2 * L - 2);
+    const int64_t item = item0 + (threadIdx.x >> 2);
     if (item >= ngroups * kc) return;
     const int col = int(item % kc);
     const int64_t g = item / kc;
@@ -296,13 +306,14 @@ __global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin
     for (int w = 0; w < 4; ++w) {
         const float2* x = xin + (ADJ ? high(w) : low(w)) * R;
         const int o = ADJ ? w : u, c = ADJ ? u : w;
-        const float2* ph = Ph + ((g * 4 + o) * 4 + c) * R;
+        const float2* ph = staged ? phs + ((g - g0) * 16 + o * 4 + c) * R : Ph + ((g * 4 + o) * 4 + c) * R;
+        auto phv = [&](int i) { return staged ? ph[i] : __ldg(ph + i); };
         float2 xv[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) xv[t] = __ldg(x + t);
         if (SM) {
 #pragma unroll
-            for (int t = 0; t < R; ++t) xv[t] = ADJ ? cmulc(__ldg(ph + t), xv[t]) : cmul(__ldg(ph + t), xv[t]);
+            for (int t = 0; t < R; ++t) xv[t] = ADJ ? cmulc(phv(t), xv[t]) : cmul(phv(t), xv[t]);
             const float* Aw = A + w * R * RP;
 #pragma unroll
             for (int v = 0; v < R; ++v) acc[v] = cadd(acc[v], rowdot(Aw + v * RP, xv));
@@ -311,8 +322,8 @@ __global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin
 #pragma unroll
             for (int v = 0; v < R; ++v) {
                 const float2 tmp = rowdot(Au + v * RP, xv);
-                if (ADJ) cfmac(acc[v], __ldg(ph + v), tmp);
-                else cfma(acc[v], __ldg(ph + v), tmp);
+                if (ADJ) cfmac(acc[v], phv(v), tmp);
+                else cfma(acc[v], phv(v), tmp);
             }
         }
     }
