@@ -178,7 +178,7 @@ def parse_profile(text):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel build
 # (profiles/k_left3_bf_adjoint_N65536_k64.md): kernel name, N, columns per launch, precision.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("k_bf_left_adj", 1 << 16, 64, "fp32"): 256216320 + 490535680}
 
 
 def roofline_entry(name, per_launch_ms, nbytes, nfma, hbm_peak, peak_src, clocks, traffic=None):
