@@ -69,7 +69,7 @@ SIGNATURES = {
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2609_11520_b300.build`")
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python paper_2609_11520_b300/build.py`")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name, None)

@@ -1,6 +1,6 @@
 """Build the CUDA library libfio_b300.so in-tree for sm_103a (B300).
 
-    python -m paper_2609_11520_b300.build [--force]
+    python paper_2609_11520_b300/build.py [--force]
 
 Compiles every csrc/*.cu with nvcc into one shared library that exports the
 C ABI declared in include/fio.h.  nvcc cross-compiles, so this runs on hosts

@@ -29,7 +29,8 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_2609_11520_b300 import build
+    import __graft_entry__
+    build = __graft_entry__._build_module()
     build.build()
     lib = ctypes.CDLL(build.LIB)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
