@@ -439,14 +439,13 @@ fio_status launch_fused_pass(const fio_bf* bf, const HalfArgs& first, const Half
     // box's factor tables through L2
     dim3 gl(nchunk, 1 << bf->h), gr(nchunk, 1 << (bf->L - bf->h));
     const size_t shl = half_smem<KC>(Pl), shr = half_smem<KC>(Pr);
-    static bool attr_done = false;
-    if (!attr_done) {
+    static PerDeviceOnce attrs;
+    if (attrs.first()) {
         const int mx = 110 * 1024;
         cudaFuncSetAttribute(k_bf_left<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_bf_left<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_bf_right<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_bf_right<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr_done = true;
     }
     if (adjoint) {
         FIO_LAUNCH("k_bf_left_adj", st, k_bf_left<KC, true><<<gl, 256, shl, st>>>(first));
@@ -1130,11 +1129,10 @@ template <bool SPLIT> void set_attrs3_t() {
     cudaFuncSetAttribute(k_right3_group<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 inline void set_attrs3() {
-    static bool done = false;
-    if (done) return;
+    static PerDeviceOnce attrs;
+    if (!attrs.first()) return;
     set_attrs3_t<false>();
     set_attrs3_t<true>();
-    done = true;
 }
 
 template <bool ADJ>

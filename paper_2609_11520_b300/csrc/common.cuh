@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -126,5 +128,21 @@ inline int ilog2_exact(int64_t v) {
 }
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
+
+// One-time set-up per device (kernel attributes are per device): first() is true the
+// first time it is asked with a given device current.
+struct PerDeviceOnce {
+    std::mutex mu;
+    uint64_t done = 0;
+    bool first() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+        std::lock_guard<std::mutex> lock(mu);
+        const uint64_t bit = uint64_t(1) << dev;
+        if (done & bit) return false;
+        done |= bit;
+        return true;
+    }
+};
 
 }  // namespace fio
