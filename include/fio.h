@@ -211,14 +211,19 @@ fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int
 /* fio_set_large_node -- node-size threshold of the large-node kernels (no
  *   paper counterpart; process-wide, default 384).  HSS levels with at most 16
  *   nodes of size m >= m_min (the top levels of 2D operators, whose ranks grow
- *   like sqrt(N)) run FP64 level-3 formulations of the node steps, batched
- *   over the level's nodes: Y Omega^+ through the Gram matrix Omega Omega^*
- *   and its Cholesky factor, the rank-revealing step as a pivoted Cholesky of
- *   Z Z^* with Z = Y - (Y Omega^+) Omega truncated at the same threshold, bases
- *   orthonormalized by CholQR2, and the ULV elimination with Q = [Q1 Q2]
- *   (Q2 R = U by CholQR2, Q1 its orthonormal complement), products by ZGEMM.
- *   Mathematically these give the same HSS approximation and an exact ULV
- *   factorization; generators differ by unitary changes of basis.
+ *   like sqrt(N)) run level-3 formulations of the node steps, batched over the
+ *   level's nodes: Y Omega^+ through the Gram matrix Omega Omega^* and its
+ *   Cholesky factor; a null basis Gamma of Omega_tau from a projected Gaussian
+ *   block; the rank-revealing step as a pivoted Cholesky of (Y Gamma)^*(Y Gamma)
+ *   (the pivots of the column-pivoted QR of Y Gamma) truncated at the same
+ *   threshold; bases orthonormalized by CholQR2; the ULV elimination with
+ *   Q = [Q1 Q2] (Q2 R = U by CholQR2, Q1 its orthonormal complement).  Products
+ *   by cuBLAS GEMMs in FP32 (FP64 for the node pass when tol < 1e-4), with the
+ *   Gram matrix of Y Gamma, its pivoted Cholesky, the root and the Cholesky
+ *   factorizations of the eliminated blocks in FP64.  Mathematically these give
+ *   the same HSS approximation and an exact ULV factorization; generators differ
+ *   by unitary changes of basis, and ranks at the truncation boundary may differ
+ *   by a few.
  *   Errors: FIO_EINVAL for m_min < 1. */
 fio_status fio_set_large_node(int m_min);
 
