@@ -516,12 +516,16 @@ fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
     FIO_CUDA(cudaStreamSynchronize(st));
     bf->table_bytes = (nVP + nUP + nM + nT * int64_t(bf->C.size() + bf->B.size())) * 8 + int64_t(P.size()) * 4;
     static PerDeviceOnce attrs;
-    if (attrs.first()) {
-        FIO_CUDA(cudaFuncSetAttribute(k2_V_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemVadj)));
-        FIO_CUDA(cudaFuncSetAttribute(k2_U_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemUfwd)));
-        FIO_CUDA(cudaFuncSetAttribute(k2_M<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM)));
-        FIO_CUDA(cudaFuncSetAttribute(k2_M<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM)));
-    }
+    FIO_CUDA(attrs.run([] {
+        cudaError_t e = cudaFuncSetAttribute(k2_V_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemVadj));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k2_U_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemUfwd));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k2_M<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k2_M<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM));
+        return e;
+    }));
     return FIO_OK;
 }
 

@@ -440,13 +440,14 @@ fio_status launch_fused_pass(const fio_bf* bf, const HalfArgs& first, const Half
     dim3 gl(nchunk, 1 << bf->h), gr(nchunk, 1 << (bf->L - bf->h));
     const size_t shl = half_smem<KC>(Pl), shr = half_smem<KC>(Pr);
     static PerDeviceOnce attrs;
-    if (attrs.first()) {
+    FIO_CUDA(attrs.run([] {
         const int mx = 110 * 1024;
-        cudaFuncSetAttribute(k_bf_left<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_bf_left<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_bf_right<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_bf_right<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    }
+        cudaError_t e = cudaFuncSetAttribute(k_bf_left<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bf_left<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bf_right<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bf_right<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        return e;
+    }));
     if (adjoint) {
         FIO_LAUNCH("k_bf_left_adj", st, k_bf_left<KC, true><<<gl, 256, shl, st>>>(first));
         FIO_LAUNCH("k_bf_right_adj", st, k_bf_right<KC, true><<<gr, 256, shr, st>>>(second));
@@ -1117,27 +1118,30 @@ inline size_t smem3(int P) {
 }
 constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float);
 
-template <bool SPLIT> void set_attrs3_t() {
+template <bool SPLIT> cudaError_t set_attrs3_t() {
     const int mx = int(kSmem3Max);
-    cudaFuncSetAttribute(k_left3<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3_group<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_left3_group<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3_group<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_right3_group<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const void* fns[] = {(const void*)k_left3<true, SPLIT>,        (const void*)k_left3<false, SPLIT>,
+                         (const void*)k_right3<true, SPLIT>,       (const void*)k_right3<false, SPLIT>,
+                         (const void*)k_left3_group<true, SPLIT>,  (const void*)k_left3_group<false, SPLIT>,
+                         (const void*)k_right3_group<true, SPLIT>, (const void*)k_right3_group<false, SPLIT>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
-inline void set_attrs3() {
+inline fio_status set_attrs3() {
     static PerDeviceOnce attrs;
-    if (!attrs.first()) return;
-    set_attrs3_t<false>();
-    set_attrs3_t<true>();
+    FIO_CUDA(attrs.run([] {
+        const cudaError_t e = set_attrs3_t<false>();
+        return e == cudaSuccess ? set_attrs3_t<true>() : e;
+    }));
+    return FIO_OK;
 }
 
 template <bool ADJ>
 fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    set_attrs3();
+    FIO_TRY(set_attrs3());
     const int P = 1 << (bf->L - bf->h), KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
     const char* nm = ADJ ? "k_bf_left_adj" : "k_bf_left_fwd";
@@ -1147,7 +1151,7 @@ fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st
 }
 template <bool ADJ>
 fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st) {
-    set_attrs3();
+    FIO_TRY(set_attrs3());
     const int P = 1 << bf->h, KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
     const char* nm = ADJ ? "k_bf_right_adj" : "k_bf_right_fwd";
@@ -1214,7 +1218,7 @@ size_t bf_group_args_size() { return sizeof(HalfArgs); }
 // Launch the two grouped halves (device copies of the tables of bf_group_tables).
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
                            const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st) {
-    v3::set_attrs3();
+    FIO_TRY(v3::set_attrs3());
     const HalfArgs* la = static_cast<const HalfArgs*>(dleft_args);
     const HalfArgs* ra = static_cast<const HalfArgs*>(dright_args);
     const size_t sm = v3::kSmem3Max;

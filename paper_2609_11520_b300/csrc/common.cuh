@@ -129,19 +129,25 @@ inline int ilog2_exact(int64_t v) {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
-// One-time set-up per device (kernel attributes are per device): first() is true the
-// first time it is asked with a given device current.
+// One-time set-up per device (kernel attributes are per device).  run(f) calls f()
+// with the device current the first time it is asked on that device, under a lock, so
+// that no other host thread gets past run() on that device before f() has finished; the
+// device counts as done only when f() returned cudaSuccess (a failed set-up is retried
+// on the next call and its error is returned).
 struct PerDeviceOnce {
     std::mutex mu;
     uint64_t done = 0;
-    bool first() {
+    template <class F> cudaError_t run(F f) {
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return f();
         std::lock_guard<std::mutex> lock(mu);
         const uint64_t bit = uint64_t(1) << dev;
-        if (done & bit) return false;
-        done |= bit;
-        return true;
+        if (done & bit) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done |= bit;
+        return e;
     }
 };
 

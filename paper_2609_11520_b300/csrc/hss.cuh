@@ -26,7 +26,10 @@ struct fio_hss {
 
 namespace fio {
 // Large nodes (dense64.cu): levels with at most 16 nodes of size m >= the
-// threshold (default 384, fio_set_large_node) run FP64 level-3 formulations.
+// threshold (default 384, fio_set_large_node) run level-3 formulations in mixed
+// precision: FP32 bulk products of the node pass, postprocessing and ULV when the
+// HSS tolerance is >= 1e-4 (FP64 node pass below it); FP64 Gram matrix and pivoted
+// Cholesky of the rank-revealing step, root, eliminated-block Cholesky and merge.
 struct BigScratch;
 BigScratch* big_scratch_new();
 void big_scratch_free(BigScratch* b);

@@ -1,5 +1,7 @@
-"""Large-node kernels (FP64 level-3 formulations for HSS levels with few, large
-nodes) against the same references as the one-CTA kernels.
+"""Large-node kernels (level-3 formulations for HSS levels with few, large nodes:
+FP32 bulk products at tol >= 1e-4, FP64 node pass below it, FP64 Gram/pivoted
+Cholesky, root, eliminated-block Cholesky and merge) against the same
+references as the one-CTA kernels.
 
 The threshold is lowered to 2 so that the large-node path runs on small cases
 whose exact answers are known: generator-built HSS matrices (matvec, ULV solve
@@ -52,29 +54,33 @@ def test_blackbox_large_recovers_exact_hss(large, N, leaf, ranks):
     base.test_blackbox_recovers_exact_hss(N, leaf, ranks)
 
 
-def test_fio_pipeline_large(large):
-    """1D, N = 1024, leaf 64, tol 1e-3, every level on the large-node kernels.  Ranks here are
-    2..4 with pivots within 0.9..1.4 x the threshold, so which side of the cut a rank falls on
-    depends on the null basis (the oracle's Householder basis vs an orthonormalized Gaussian
-    one): e_cHSS and e_direct within 5x the oracle's, and two refinement steps within 2x."""
+@pytest.mark.parametrize("tol", [1e-4, 3e-3])
+def test_fio_pipeline_large(large, tol):
+    """1D, N = 1024, leaf 64, every level on the large-node kernels.  The large-node path reveals
+    ranks with a random orthonormal null basis instead of the oracle's Householder one, so a pivot
+    that lies close to the truncation threshold can fall on either side of it.  At tol 1e-3 some
+    pivots of this operator lie within 0.9..1.4 x the threshold; at the two tolerances used here
+    none lies within 0.7..1.6 x (oracle pivots, ranks 4 and 2 per level), so the ranks are
+    decided the same way on both sides and the bound is the benchmark spec's 2x."""
     from oracle.problem import Phase
     from oracle.solver import FIOSolver
     from paper_2609_11520_b300 import BF, HSS, fio_solve
-    n, leaf, tol, p, seed = 1024, 64, 1e-3, 10, 1
+    n, leaf, p, seed = 1024, 64, 10, 1
     S = FIOSolver(Phase("cabs"), n, 16, leaf, p, tol, seed)
     bf = BF(n, 16)
     g = HSS.from_samples(bf=bf, leaf=leaf, oversample=p, tol=tol, seed=seed)
+    assert g.info()["ranks"] == S.hss.ranks, (g.info()["ranks"], S.hss.ranks)
     x = crandn(n, 2, seed=3)
     GKx = S.bf.adjoint(S.bf.apply(x))
     e_hss_o = rel(S.hss.matvec(x), GKx)
     e_hss_g = rel(to_np(g.matvec(to_dev(x))), GKx)
-    assert e_hss_g <= 5 * e_hss_o + 1e-5, (e_hss_g, e_hss_o, g.info()["ranks"], S.stats["ranks"])
+    assert e_hss_g <= 2 * e_hss_o + 1e-5, (e_hss_g, e_hss_o, g.info()["ranks"], S.stats["ranks"])
     g.factor()
     f = crandn(n, 4, seed=0)
     u = S.bf.apply(f)
     e_o = rel(S.solve(u), f)
     e_g = rel(to_np(fio_solve(bf, g, to_dev(u))), f)
-    assert e_g <= 5 * e_o + 1e-5, (e_g, e_o)
+    assert e_g <= 2 * e_o + 1e-5, (e_g, e_o)
     e_r = rel(to_np(fio_solve(bf, g, to_dev(u), refine_steps=2)), f)
     assert e_r <= 2 * e_o + 1e-5, (e_r, e_o)
 
