@@ -455,6 +455,54 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """One stage of the online path, repeated between cudaProfilerStart / Stop so that
+    `ncu --profile-from-start off` captures only those launches.  Cases: bf_adjoint, bf_forward
+    (1D, N = --n, k = --k columns), hss_solve, fio_solve (1D operator with its HSS), bf2d_adjoint,
+    bf2d_forward (2D elliptic phase, n = --n per dimension).  --path picks the BF kernels
+    (auto, per_level, fused, fused_v2, fused_simt), --precision fp32 or split_bf16.
+    Prints the mean CUDA-event time per repetition."""
+    import torch
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    torch.cuda.set_device(0)
+    case = args.profile_case
+    two_d = case.startswith("bf2d")
+    n = args.n if args.n else (256 if two_d else 1 << 16)
+    bf = BF(n, 25, "elliptic2d") if two_d else BF(n, 16)
+    hss = None
+    if case in ("hss_solve", "fio_solve"):
+        hss = HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=2).factor()
+    if not two_d:
+        bf.set_path(args.path).set_precision(args.precision)
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy((rng.standard_normal((args.k, bf.n)) + 1j * rng.standard_normal((args.k, bf.n)))
+                         .astype(np.complex64)).cuda()
+    Y = torch.empty_like(X)
+
+    def run():
+        if case in ("bf_adjoint", "bf2d_adjoint"):
+            bf.apply(X, adjoint=True, out=Y)
+        elif case in ("bf_forward", "bf2d_forward"):
+            bf.apply(X, out=Y)
+        elif case == "hss_solve":
+            hss.solve(X, out=Y)
+        else:
+            fio_solve(bf, hss, X, out=Y)
+
+    run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    a.record()
+    for _ in range(args.reps):
+        run()
+    b.record()
+    torch.cuda.profiler.stop()
+    torch.cuda.synchronize()
+    print(f"{case} n={n} k={args.k} path={args.path} precision={args.precision}: "
+          f"{a.elapsed_time(b) / args.reps:.4f} ms per repetition")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,7 +514,15 @@ def main():
     ap.add_argument("--n2d", type=int, default=64)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["bf_adjoint", "bf_forward", "hss_solve", "fio_solve", "bf2d_adjoint", "bf2d_forward"])
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--path", default="auto")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched1d":

@@ -123,17 +123,25 @@ fio_status bf_apply_noalloc(const fio_bf* bf, const void* X, void* Y, int64_t ld
  *   results agree to FP32 rounding):  0 = automatic (fused two-pass kernels
  *   where r = 16 and n >= 64, else per-level kernels), 1 = one kernel per
  *   factor (per-level), 2 = fused two-pass (tables staged through shared
- *   memory where each half has 64..256 pairs per CTA), 3 = fused two-pass
- *   without the staging.  FIO_EINVAL where a fused path is unsupported
- *   (2D handles: per-level kernels only). */
+ *   memory where each half has 64..512 pairs per CTA; the transfer levels on
+ *   the tensor cores), 3 = fused two-pass without the staging, 4 = the staged
+ *   fused kernels with the FP32 transfer levels on the CUDA cores instead of
+ *   the tensor cores.  FIO_EINVAL where a fused path is unsupported (2D
+ *   handles: per-level kernels only). */
 fio_status bf_set_path(fio_bf* bf, int path);
 
-/* bf_set_precision -- arithmetic of the transfer levels of bf_apply:
- *   FIO_FP32 (0, default) FP32 FMA; FIO_SPLIT_BF16 (1) tensor-core products
- *   on BF16 operands split as v = hi + lo (hi*hi + hi*lo + lo*hi, FP32
- *   accumulation), phases and the middle factor in FP32; relative error of
- *   an apply about 1e-5.  Split precision runs on the staged fused kernels
- *   (r = 16, 2^12 <= n <= 2^18; FIO_EINVAL otherwise) whatever bf_set_path chose. */
+/* bf_set_precision -- arithmetic of the transfer levels of bf_apply (the real
+ *   Lagrange products of Eq. 2.4-2.6, shared by every box of a level):
+ *   FIO_FP32 (0, default) FP32 accuracy: on the staged fused kernels these
+ *   products run on the tensor cores (tcgen05, FP32 accumulation in tensor
+ *   memory) with both operands split into FP16 parts v = hi + lo (three
+ *   products hi*hi + hi*lo + lo*hi; every row scaled by an exact power of two
+ *   into the FP16 range), elsewhere (and with path 4) FP32 FMA on the CUDA
+ *   cores; FIO_SPLIT_BF16 (1) the same tensor-core products on BF16 parts
+ *   (8 + 8 bits, relative error of an apply about 1e-5).  Phases and the
+ *   middle factor are FP32 in both.  Split precision runs on the staged fused
+ *   kernels (r = 16, 2^12 <= n <= 2^18; FIO_EINVAL otherwise) whatever
+ *   bf_set_path chose. */
 typedef enum { FIO_FP32 = 0, FIO_SPLIT_BF16 = 1 } fio_precision;
 fio_status bf_set_precision(fio_bf* bf, int precision);
 
@@ -205,7 +213,7 @@ fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int
  *   (built by hss_build_from_samples from this BF) is over the frequency
  *   index in quadtree (Morton) order; the solve runs in that order and F is
  *   returned in lexicographic order. */
-fio_status fio_solve(fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
+fio_status fio_solve(const fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
                      int refine_steps, void* stream);
 
 /* fio_set_large_node -- node-size threshold of the large-node kernels (no
@@ -259,6 +267,12 @@ fio_status fio_batch_solve(fio_batch* batch, const void* const* U, void* const* 
 fio_status fio_batch_autotune(fio_batch* batch, const void* const* U, void* const* F, const int* k, int reps,
                               void* stream, char* report, int64_t len);
 void fio_batch_free(fio_batch* batch);
+
+/* fio_device_status -- FIO_ETIMEOUT if a bounded wait inside a tensor-core
+ *   kernel (an mbarrier wait for its MMAs) ran out since the last call, which
+ *   marks that launch's results invalid; the flag is cleared.  Synchronizes
+ *   with the device (reads a device flag).  No paper counterpart. */
+fio_status fio_device_status(void);
 
 /* fio_last_error -- message of the last failing call on this thread. */
 const char* fio_last_error(void);

@@ -61,6 +61,7 @@ SIGNATURES = {
                                  ctypes.c_char_p, I64]),
     "fio_batch_free": (None, [P]),
     "fio_last_error": (ctypes.c_char_p, []),
+    "fio_device_status": (I32, []),
     "fio_profile_enable": (I32, [I32]),
     "fio_set_large_node": (I32, [I32]),
     "fio_profile_report": (I32, [ctypes.c_char_p, I64]),

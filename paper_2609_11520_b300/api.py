@@ -12,7 +12,7 @@ import torch
 from . import _lib
 from ._lib import FioError, check, lib
 
-__all__ = ["BF", "HSS", "Batch", "fio_solve", "FioError"]
+__all__ = ["BF", "HSS", "Batch", "fio_solve", "device_status", "FioError"]
 
 
 def _stream(stream=None):
@@ -54,13 +54,18 @@ class BF:
     def handle(self):
         return self._h
 
+    PATHS = {"auto": 0, "per_level": 1, "fused": 2, "fused_v2": 3, "fused_simt": 4}
+
     def set_path(self, path):
-        """0 automatic, 1 per-level kernels, 2 fused two-pass kernels, 3 fused without table staging."""
-        check(lib.bf_set_path(self._h, int({"auto": 0, "per_level": 1, "fused": 2, "fused_v2": 3}.get(path, path))))
+        """0 automatic, 1 per-level kernels, 2 fused two-pass kernels (transfer levels on the tensor
+        cores), 3 fused without table staging, 4 ("fused_simt") the staged fused kernels with the
+        FP32 transfer levels on the CUDA cores."""
+        check(lib.bf_set_path(self._h, int(self.PATHS.get(path, path))))
         return self
 
     def set_precision(self, precision):
-        """"fp32" (default) or "split_bf16" (tensor-core transfer levels, BF16 hi + lo)."""
+        """"fp32" (default; FP32 accuracy, tensor-core transfer levels on FP16 hi + lo parts) or
+        "split_bf16" (tensor-core transfer levels on BF16 hi + lo parts)."""
         check(lib.bf_set_precision(self._h, int({"fp32": 0, "split_bf16": 1}.get(precision, precision))))
         return self
 
@@ -168,6 +173,12 @@ class HSS:
         if h is not None and h.value:
             lib.hss_free(h)
             self._h = ctypes.c_void_p()
+
+
+def device_status():
+    """Raise FioError (FIO_ETIMEOUT) if a bounded wait inside a tensor-core kernel ran out since
+    the last call; synchronizes with the device."""
+    check(lib.fio_device_status())
 
 
 def fio_solve(bf, hss, U, out=None, refine_steps=0, stream=None):

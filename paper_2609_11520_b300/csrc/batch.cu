@@ -31,7 +31,7 @@ struct fio_batch {
     std::vector<int> keyK;
     fio::DevBuf T, mid, ulvws;                // K~^* U, BF middle states, ULV solve vectors (per operator)
     std::vector<int> fallback;                // operators not covered by the grouped BF kernels
-    int split = 0;                            // precision of the grouped BF kernels
+    int bfmode = 0;                           // transfer-level mode of the grouped BF kernels (bf_fused_mode)
     std::vector<size_t> Toff;
     fio::DevBuf dargs_l, dargs_r, ditems_l, ditems_r;
     int nl = 0, nr = 0;
@@ -81,17 +81,17 @@ fio_status plan(fio_batch* b, const void* const* U, void* const* F, const int* k
     // grouped BF adjoint
     std::vector<BfGroupOp> ops;
     b->fallback.clear();
-    b->split = -1;   // the grouped launch runs one precision: the first covered operator's
+    b->bfmode = -1;   // the grouped launch runs one transfer-level mode: the first covered operator's
     for (int i = 0; i < n; ++i) {
         if (k[i] == 0) continue;
-        if (bf_v3_ok(b->bfs[i]) && b->split < 0) b->split = b->bfs[i]->split ? 1 : 0;
-        if (bf_v3_ok(b->bfs[i]) && (b->bfs[i]->split ? 1 : 0) == b->split)
+        if (bf_v3_ok(b->bfs[i]) && b->bfmode < 0) b->bfmode = bf_fused_mode(b->bfs[i], -1);
+        if (bf_v3_ok(b->bfs[i]) && bf_fused_mode(b->bfs[i], -1) == b->bfmode)
             ops.push_back(BfGroupOp{b->bfs[i], static_cast<const float2*>(U[i]), b->T.as<float2>() + b->Toff[i],
                                     b->mid.as<float2>() + moff[i], k[i]});
         else
             b->fallback.push_back(i);
     }
-    if (b->split < 0) b->split = 0;
+    if (b->bfmode < 0) b->bfmode = 0;
     std::vector<unsigned char> la, ra;
     std::vector<int4> li, ri;
     bf_group_tables(ops, 1, la, li, ra, ri);
@@ -158,7 +158,7 @@ fio_status plan(fio_batch* b, const void* const* U, void* const* F, const int* k
 
 fio_status launch_grouped(fio_batch* b, cudaStream_t st) {
     FIO_TRY(bf_group_launch(b->dargs_l.p, b->ditems_l.as<int4>(), b->nl, b->dargs_r.p, b->ditems_r.as<int4>(), b->nr, 1,
-                            b->split, st));
+                            b->bfmode, st));
     for (int i : b->fallback)
         FIO_TRY(bf_apply(b->bfs[i], b->keyU[i], b->T.as<float2>() + b->Toff[i], b->bfs[i]->n, b->keyK[i], 1, st));
     const int4* it = b->ditems.as<int4>();

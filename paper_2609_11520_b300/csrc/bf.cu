@@ -471,10 +471,11 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
 }
 
 namespace fio {
-fio_status bf_apply_ord(fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
-                        cudaStream_t st) {
-    if (!bf) return fail(FIO_EINVAL, "bf_apply: null handle");
-    if (bf->d == 1) return bf_apply(bf, X, Y, ld, k, adjoint, st);
+fio_status bf_apply_ord(const fio_bf* bfc, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
+                        cudaStream_t st, int prec) {
+    if (!bfc) return fail(FIO_EINVAL, "bf_apply: null handle");
+    if (bfc->d == 1) return bf_apply_prec(bfc, X, Y, ld, k, adjoint, prec, st);
+    fio_bf* bf = const_cast<fio_bf*>(bfc);   // the 2D path only grows the handle's scratch
     if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
@@ -491,16 +492,20 @@ fio_status bf_apply_ord(fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
 }
 }  // namespace fio
 
-extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream) {
-    if (!bf) return fail(FIO_EINVAL, "bf_apply: null handle");
-    if (k < 0 || ld < bf->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
+namespace fio {
+// bf_apply with an explicit precision request (-1: the handle's setting); the handle's
+// settings are not modified, only its scratch grows.
+fio_status bf_apply_prec(const fio_bf* bfc, const float2* X, float2* Y, int64_t ld, int k, int adjoint, int prec,
+                         cudaStream_t st) {
+    if (!bfc) return fail(FIO_EINVAL, "bf_apply: null handle");
+    if (k < 0 || ld < bfc->n) return fail(FIO_EINVAL, "bf_apply: need k >= 0 and ld >= N");
     if (k == 0) return FIO_OK;
     if (!X || !Y) return fail(FIO_EINVAL, "bf_apply: null vector");
-    cudaStream_t st = as_stream(stream);
-    if (bf->d == 2)
-        return bf_apply_ord(bf, static_cast<const float2*>(X), static_cast<float2*>(Y), ld, k, adjoint, false, st);
+    if (bfc->d == 2) return bf_apply_ord(bfc, X, Y, ld, k, adjoint, false, st, prec);
+    fio_bf* bf = const_cast<fio_bf*>(bfc);
+    const bool split = prec < 0 ? bf->split : prec == 1;
     const int64_t stateN = int64_t(bf->n) * bf->r;
-    const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || bf->split);
+    const bool fused = bf_fused_ok(bf) && (!bf->force_unfused || split);
     // column chunk: at most 64 columns or 1 GiB of state, whichever is smaller
     const int nstate = fused ? 1 : 2;
     int kc = int(std::min<int64_t>(k, std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(1) << 30) / (nstate * stateN * 8)))));
@@ -509,20 +514,35 @@ extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, i
     float2* s1 = s0 + stateN * kc;
     for (int c0 = 0; c0 < k; c0 += kc) {
         int cc = std::min(kc, k - c0);
-        const float2* Xc = reinterpret_cast<const float2*>(X) + c0 * ld;
-        float2* Yc = reinterpret_cast<float2*>(Y) + c0 * ld;
-        if (fused) FIO_TRY(bf_apply_fused(bf, Xc, Yc, ld, cc, adjoint, s0, st));
+        const float2* Xc = X + c0 * ld;
+        float2* Yc = Y + c0 * ld;
+        if (fused) FIO_TRY(bf_apply_fused(bf, Xc, Yc, ld, cc, adjoint, s0, st, prec));
         else FIO_TRY(bf_apply_cols(bf, Xc, Yc, ld, cc, adjoint, s0, s1, st));
     }
     return FIO_OK;
 }
+}  // namespace fio
+
+extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream) {
+    return bf_apply_prec(bf, static_cast<const float2*>(X), static_cast<float2*>(Y), ld, k, adjoint, -1,
+                         as_stream(stream));
+}
 
 extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
-    if (!bf || path < 0 || path > 3) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
+    if (!bf || path < 0 || path > 4) return fail(FIO_EINVAL, "bf_set_path: bad handle or path");
     if (bf->d == 2 && path >= 2) return fail(FIO_EINVAL, "bf_set_path: 2D handles run the per-level kernels only");
     if (path >= 2 && !bf_fused_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: fused apply needs r = 16 and n >= 64");
+    if (path == 4 && !bf_v3_ok(bf)) return fail(FIO_EINVAL, "bf_set_path: staged fused kernels need 2^12 <= n <= 2^18");
     bf->force_unfused = (path == 1);
     bf->fused_v2 = (path == 3);
+    bf->simt = (path == 4);
+    return FIO_OK;
+}
+
+extern "C" fio_status fio_device_status(void) {
+    const int v = tc_wait_timeouts();
+    if (v < 0) return fail(FIO_ECUDA, "fio_device_status: reading the device flag failed");
+    if (v > 0) return fail(FIO_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (results of that launch are invalid)");
     return FIO_OK;
 }
 

@@ -37,7 +37,8 @@ struct fio_bf {
     int64_t table_bytes = 0;
     bool force_unfused = false;    // use the per-level kernels even where the fused pass applies
     bool fused_v2 = false;         // fused pass without shared-memory table staging
-    bool split = false;            // transfer levels in split BF16 on the tensor cores (staged fused path)
+    bool split = false;            // split-precision setting: transfer levels with BF16 hi + lo parts
+    bool simt = false;             // FP32 setting on the CUDA cores instead of the tensor cores (staged fused path)
     int64_t N() const { return int64_t(n); }
     size_t pv_off() const { return 0; }
     size_t pu_off() const { return size_t(lsV) * r; }
@@ -49,8 +50,17 @@ namespace fio {
 bool bf_fused_ok(const fio_bf* bf);
 bool bf_v3_ok(const fio_bf* bf);   // staged fused kernels apply (64..512 pairs per CTA)
 int bf_fused_kc(const fio_bf* bf);
+// prec: -1 the handle's precision setting, 0 FP32, 1 split BF16.
 fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, float2* mid,
-                          cudaStream_t st);
+                          cudaStream_t st, int prec = -1);
+// Transfer-level mode of the staged fused kernels (0 CUDA cores, 1 tensor cores FP16 parts,
+// 2 tensor cores BF16 parts) for the given precision request.
+int bf_fused_mode(const fio_bf* bf, int prec);
+// Whether a bounded wait of a tensor-core kernel ran out since the last call (cleared); -1 on error.
+int tc_wait_timeouts();
+// bf_apply with an explicit precision (prec as above): the handle is not modified.
+fio_status bf_apply_prec(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, int prec,
+                         cudaStream_t st);
 // Grouped fused apply over several operators (bf_v3_ok each): host tables, then
 // launches that only read device copies of them.
 struct BfGroupOp {
@@ -65,7 +75,7 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
                      std::vector<int4>& right_items);
 size_t bf_group_args_size();
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
-                           const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st);
+                           const int4* dright_items, int nright, int adjoint, int mode, cudaStream_t st);
 // Host Lagrange polynomial l_k(u) on the nodes t[0..r).
 double lagrange_host(const double* t, int r, int k, double u);
 // 2D handles (d = 2, r = 25; bf2d.cu).  The same fio_bf fields hold the 2D
@@ -77,8 +87,8 @@ fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t
 fio_status bf2d_unmorton(const fio_bf* bf, const float2* Xm, float2* X, int64_t ld, int k, cudaStream_t st);
 // bf_apply with the frequency vectors of a 2D handle in quadtree (Morton)
 // order when `morton` is set (the order of the HSS of K~^* K~); 1D: bf_apply.
-fio_status bf_apply_ord(fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
-                        cudaStream_t st);
+fio_status bf_apply_ord(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,
+                        cudaStream_t st, int prec = -1);
 // Y = K~ X or K~^* X for kc columns using states s0, s1 (each N*r*kc complex).
 fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint,
                          float2* s0, float2* s1, cudaStream_t st);

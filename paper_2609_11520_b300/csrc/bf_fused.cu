@@ -22,10 +22,13 @@
 // Threads enumerate quads by physical slot, so that consecutive threads touch
 // consecutive slots, and shared memory is XOR-swizzled in 16-byte chunks.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "bf.cuh"
+#include "tc.cuh"
 
 namespace fio {
 namespace {
@@ -245,7 +248,7 @@ struct HalfArgs {
     int pu_off, pc_off;
     Tabs tab;            // left: E tables by s - h ; right: F tables by s - sV
     int n, L, h, sU, sV, k;
-    int split;           // transfer levels on the tensor cores, BF16 hi+lo (v3 kernels only)
+    int mode;            // transfer levels of the staged kernels: kSimt, kTcF16 or kTcBF16
 };
 
 // Left half, one CTA per space box tau_h (blockIdx.x) and KC columns (blockIdx.y).
@@ -616,134 +619,270 @@ __device__ void level3(float2* S, const float* sPc, const float4* ph, int s, con
     store_pair(Sc, o ? base + half : base, y);
 }
 
-// ---------------------------------------------------------------- split BF16
-// Transfer level on the tensor cores.  The real Lagrange products of a level
-// are GEMMs with a matrix shared by every quad:
-//   MS:  H_o = P_o X            (16 x 16) x (16 x columns), columns = (quad, e, re/im)
-//   SM:  Y_o = [P_0^T P_1^T] G_o (16 x 32) x (32 x columns), G = phase-scaled inputs
-// computed with mma.sync m16n8k16 on BF16 operands split as v = hi + lo
-// (three products hi*hi + hi*lo + lo*hi, FP32 accumulation); the complex phase
-// products stay in FP32.  A warp tile is two quads of one column: 8 GEMM
-// columns = 4 complex vectors.  Fragment coordinates (PTX m16n8k16): lane =
-// 4 g + t; A rows g, g+8 x cols 2t, 2t+1, 2t+8, 2t+9; B rows (k) 2t, 2t+1,
-// 2t+8, 2t+9 x col g; D rows g, g+8 x cols 2t, 2t+1.
-struct SplitFrag {
-    unsigned hi[4], lo[4];
+// ---------------------------------------------------------------- tensor cores
+// Transfer level on the 5th-generation tensor cores (tcgen05).  The real
+// Lagrange products of a level are GEMMs with one matrix shared by every quad
+// of the CTA; one GEMM row per thread (task (column, quad, o)), 4 tiles of
+// M = 128 rows per CTA:
+//   SM: A row = [g_0 | g_1],  g_e[t] = Phi(o,e,t) x_e[t]  (K = 2 e x 16 t x re/im = 64)
+//       B[(j, re/im)][(e, t, re/im)] = Pc[e][t][j]       ->  D row = y_o (N = 32)
+//   MS: A row = [J_o x_0 | J_o x_1] (J_o reverses t when o = 0), two products
+//       with B[(i, re/im)][(t, re/im)] = Pc[1][i][t]  ->  D_e row = J_o P_o x_e
+//       (N = 32 each), since P_0 = J P_1 J (Chebyshev nodes are symmetric);
+//       the epilogue reverses back and forms y_o = sum_e Phi(o,e,i) D_e.
+// Real and imaginary parts ride as separate K / N indices (B is zero between
+// them).  FP32 accuracy comes from a three-term split v = hi + lo of both
+// operands, D = A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in
+// TMEM: FP16 parts (11 + 11 bits) with every row scaled by a power of two that
+// puts its largest entry in [2^14, 2^15) (exact; undone in the epilogue), or
+// BF16 parts (8 + 8 bits, no scaling) for the split-precision setting.
+// A rows are written to TMEM with tcgen05.st, B sits in shared memory, and one
+// thread issues the MMAs and commits them to an mbarrier.
+// TMEM columns of tile t: A_hi [128t, +32), A_lo [128t + 32, +32), D [128t + 64, +64).
+constexpr int kSimt = 0, kTcF16 = 1, kTcBF16 = 2;
+constexpr int kTmemCols = 512;
+constexpr uint32_t kBBytesSM = 32 * 64 * 2, kBBytesMS = 32 * 32 * 2;   // one of hi / lo
+
+struct Tc {
+    uint32_t tmem;     // TMEM base address
+    uint64_t* mbar;    // MMA completion
+    int* fail;         // shared flag: a bounded wait ran out
+    uint32_t phase;    // parity of the next completion of mbar
+    uint32_t bsm;      // shared address of B_hi; B_lo follows at + bbytes
+    uint32_t bbytes;
 };
 
-__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // a in the low half
-    return *reinterpret_cast<unsigned*>(&v);
-}
-// hi / lo BF16 parts of a pair of floats
-__device__ __forceinline__ void split2(float a, float b, unsigned& hi, unsigned& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    hi = *reinterpret_cast<const unsigned*>(&h);
-    lo = pack_bf16(a - hf.x, b - hf.y);
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// A fragment of a 16 x 16 matrix given by elem(row, col)
-template <class F> __device__ __forceinline__ SplitFrag afrag(F elem) {
-    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
-    SplitFrag f;
-    split2(elem(g, 2 * t), elem(g, 2 * t + 1), f.hi[0], f.lo[0]);
-    split2(elem(g + 8, 2 * t), elem(g + 8, 2 * t + 1), f.hi[1], f.lo[1]);
-    split2(elem(g, 2 * t + 8), elem(g, 2 * t + 9), f.hi[2], f.lo[2]);
-    split2(elem(g + 8, 2 * t + 8), elem(g + 8, 2 * t + 9), f.hi[3], f.lo[3]);
-    return f;
-}
-__device__ __forceinline__ void mma3(float (&d)[4], const SplitFrag& a, unsigned bh0, unsigned bh1, unsigned bl0,
-                                     unsigned bl1) {
-    mma_bf16(d, a.hi, bh0, bh1);
-    mma_bf16(d, a.hi, bl0, bl1);
-    mma_bf16(d, a.lo, bh0, bh1);
-}
-__device__ __forceinline__ float2 chunk_elem(const float4* row, int sw8, int i) {
-    const float4 v = row[(i >> 1) ^ sw8];
-    return (i & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+template <bool BF> struct Half16;
+template <> struct Half16<false> {
+    using T2 = __half2;
+    static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+    static __device__ __forceinline__ float2 unpack(T2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ uint16_t one(float a) { return __half_as_ushort(__float2half_rn(a)); }
+    static __device__ __forceinline__ float back(uint16_t v) { return __half2float(__ushort_as_half(v)); }
+};
+template <> struct Half16<true> {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    static __device__ __forceinline__ float2 unpack(T2 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ uint16_t one(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    static __device__ __forceinline__ float back(uint16_t v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
+};
+
+// hi / lo parts of (a, b) as two packed 16-bit pairs
+template <bool BF> __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    using H = Half16<BF>;
+    const typename H::T2 h = H::pack(a, b);
+    const float2 f = H::unpack(h);
+    const typename H::T2 l = H::pack(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// fa[0..1]: MS -> P_0, P_1 (rows i, cols t);  SM -> P_0^T, P_1^T (rows j, cols t).
-template <bool LEFT, bool MS, bool ADJ>
-__device__ void level3_tc(float2* S, const SplitFrag (&fa)[2], const float4* ph, int s, const Geo& g) {
+// Power-of-two row scale for the FP16 parts: largest |entry| (bounded by mx) into [2^14, 2^15).
+__device__ __forceinline__ void row_scale(float mx, float& sc, float& isc) {
+    const int ex = int((__float_as_uint(mx) >> 23) & 0xFF);
+    const int se = ex == 0 ? 127 : min(max(268 - ex, 1), 253);
+    sc = __uint_as_float(uint32_t(se) << 23);
+    isc = __uint_as_float(uint32_t(254 - se) << 23);
+}
+
+// Build B_hi / B_lo of the level form in shared memory (canonical K-major layout,
+// LBO = 128 B between core matrices along K, SBO = K / 8 * 128 B between 8-row groups).
+template <bool MS, bool BF> __device__ void build_b(unsigned char* bs, const float* sPc) {
+    using H = Half16<BF>;
+    constexpr int K = MS ? 32 : 64, N = 32;
+    uint16_t* hi = reinterpret_cast<uint16_t*>(bs);
+    uint16_t* lo = reinterpret_cast<uint16_t*>(bs + N * K * 2);
+    for (int e = threadIdx.x; e < N * K; e += blockDim.x) {
+        const int n = e / K, k = e % K;
+        const int jn = n >> 1, pn = n & 1;
+        float v = 0.f;
+        if (MS) {   // k = (t, re/im)
+            const int t = k >> 1, pk = k & 1;
+            if (pk == pn) v = sPc[PCS + jn * R + t];
+        } else {    // k = (e, t, re/im)
+            const int ee = k >> 5, t = (k >> 1) & (R - 1), pk = k & 1;
+            if (pk == pn) v = sPc[ee * PCS + t * R + jn];
+        }
+        const uint16_t h = H::one(v);
+        const uint16_t l = H::one(v - H::back(h));
+        const int off = (n >> 3) * (K / 8) * 64 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);   // in 16-bit elements
+        hi[off] = h;
+        lo[off] = l;
+    }
+}
+
+__device__ int g_tc_wait_timeout = 0;
+
+// B operands of the tensor-core levels: the first 128-byte boundary after `after`.
+__device__ __forceinline__ unsigned char* tc_bsm(const float* after) {
+    const uintptr_t p = reinterpret_cast<uintptr_t>(after);
+    return reinterpret_cast<unsigned char*>((p + 127) & ~uintptr_t(127));
+}
+
+template <bool LEFT, bool MS, bool ADJ, bool BF>
+__device__ void level3_tc(float2* S, const float4* ph, int s, const Geo& g, Tc& tc) {
     const int P = g.P;
     const int W = LEFT ? g.L - s : g.h - s;
     const int half = 1 << (W - 1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gg = lane >> 2, t = lane & 3;
-    const int ntile = (P / 4) * g.KC;
-    for (int tile = warp; tile < ntile; tile += NT / 32) {
-        const int col = tile / (P / 4), qp = tile % (P / 4);
-        float2* Sc = S + col * P * R;
-        auto basef = [&](int qi) { return ((qi >> (W - 1)) << W) | (qi & (half - 1)); };
-        // ---- B fragments (this lane's GEMM column gg: vector gg >> 1, part gg & 1)
-        const int v = gg >> 1, part = gg & 1;
-        const int qb = 2 * qp + (v >> 1);
-        const int vb = v & 1;   // MS: input half e; SM: output half o
-        const int bq = basef(qb);
-        unsigned bh[2][2], bl[2][2];   // [K step][register]
+    const int id = threadIdx.x;   // KC * P == NT: one GEMM row per thread
+    const int col = id >> g.lgP, rem = id & (P - 1), qi = rem >> 1, o = rem & 1;
+    const int base = ((qi >> (W - 1)) << W) | (qi & (half - 1));
+    float2* Sc = S + col * P * R;
+    const int sw8 = (qi * 2 + o) & 7;
+    const float4* r0 = ph + (qi * 4 + o * 2 + 0) * 8;   // Phi(o, e = 0, .)
+    const float4* r1 = ph + (qi * 4 + o * 2 + 1) * 8;   // Phi(o, e = 1, .)
+    const uint32_t tcol = tc.tmem + (uint32_t(id & 0x60) << 16) + uint32_t(id >> 7) * 128;
+    float sc = 1.f, isc = 1.f;
+    {
+        float2 x0[R], x1[R];
+        load_pair(Sc, base, x0);
+        load_pair(Sc, base + half, x1);
+        if (!BF) {   // |Phi| = 1: |Re g|, |Im g| <= |Re x| + |Im x|
+            float mx = 0.f;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                mx = fmaxf(mx, fabsf(x0[t].x) + fabsf(x0[t].y));
+                mx = fmaxf(mx, fabsf(x1[t].x) + fabsf(x1[t].y));
+            }
+            row_scale(mx, sc, isc);
+        }
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            if (MS && e == 1) break;
-            const int slot = bq + (MS ? vb : e) * half;
-            float2 xv[4];
-            const int tt[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+            uint32_t hi[R], lo[R];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = Sc[sw(slot, tt[u])];
-            if (!MS) {   // phase-scale first: g = Phi(o, e, t) x[e][t]
-                const int row = qb * 4 + vb * 2 + e, sw8 = (qb * 2 + vb) & 7;
+            for (int m = 0; m < R / 2; ++m) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 f = chunk_elem(ph + row * 8, sw8, tt[u]);
-                    xv[u] = ADJ ? cmulc(f, xv[u]) : cmul(f, xv[u]);
+                for (int u = 0; u < 2; ++u) {
+                    const int t = 2 * m + u;
+                    float2 v;
+                    if (MS) {
+                        const float2 a0 = e ? x1[t] : x0[t], a1 = e ? x1[R - 1 - t] : x0[R - 1 - t];
+                        v = o ? a0 : a1;
+                    } else {
+                        const float4 pq = (e ? r1 : r0)[m ^ sw8];
+                        const float2 f = u ? make_float2(pq.z, pq.w) : make_float2(pq.x, pq.y);
+                        const float2 xv = e ? x1[t] : x0[t];
+                        v = ADJ ? cmulc(f, xv) : cmul(f, xv);
+                    }
+                    split_pair<BF>(v.x * sc, v.y * sc, hi[t], lo[t]);
                 }
             }
-            float val[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) val[u] = part ? xv[u].y : xv[u].x;
-            split2(val[0], val[1], bh[e][0], bl[e][0]);
-            split2(val[2], val[3], bh[e][1], bl[e][1]);
+            tc::tmem_st16(tcol + 16 * e, hi);
+            tc::tmem_st16(tcol + 32 + 16 * e, lo);
         }
-        __syncwarp();
-        // ---- products; D columns 2t, 2t+1 = (re, im) of vector t
-        const int qd = 2 * qp + (t >> 1), vd = t & 1;
-        const int bd = basef(qd);
-        if (MS) {
+        tc::tmem_wait_st();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (id == 0 && !*tc.fail) {
+        tc::fence_after();
+        const uint32_t idesc = tc::idesc_f16(BF, 128, 32);
+        constexpr uint32_t sbo = MS ? 512 : 1024;
+#pragma unroll 1
+        for (int t4 = 0; t4 < 4; ++t4) {
+            const uint32_t A = tc.tmem + 128 * t4, D = A + 64;
+            if (MS) {
 #pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-                mma3(d, fa[o], bh[0][0], bh[0][1], bl[0][0], bl[0][1]);
-                // h[o][e = vd][i] for i = gg, gg + 8; y[o][i] = sum_e Phi(o, e, i) h[o][e][i]
-                const int row = qd * 4 + o * 2 + vd, sw8 = (qd * 2 + o) & 7;
-                const float2 f0 = chunk_elem(ph + row * 8, sw8, gg), f1 = chunk_elem(ph + row * 8, sw8, gg + 8);
-                const float2 h0 = make_float2(d[0], d[1]), h1 = make_float2(d[2], d[3]);
-                float2 z0 = ADJ ? cmulc(f0, h0) : cmul(f0, h0);
-                float2 z1 = ADJ ? cmulc(f1, h1) : cmul(f1, h1);
-                z0.x += __shfl_xor_sync(0xffffffffu, z0.x, 1);
-                z0.y += __shfl_xor_sync(0xffffffffu, z0.y, 1);
-                z1.x += __shfl_xor_sync(0xffffffffu, z1.x, 1);
-                z1.y += __shfl_xor_sync(0xffffffffu, z1.y, 1);
-                if (vd == 0) {
-                    const int so = bd + o * half;
-                    Sc[sw(so, gg)] = z0;
-                    Sc[sw(so, gg + 8)] = z1;
+                for (int e = 0; e < 2; ++e)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t bh = tc::smem_desc(tc.bsm + 256 * ks, 128, sbo);
+                        const uint64_t bl = tc::smem_desc(tc.bsm + tc.bbytes + 256 * ks, 128, sbo);
+                        const uint32_t ah = A + 16 * e + 8 * ks, al = ah + 32;
+                        tc::mma_f16_ts(D + 32 * e, ah, bh, idesc, ks);
+                        tc::mma_f16_ts(D + 32 * e, ah, bl, idesc, 1);
+                        tc::mma_f16_ts(D + 32 * e, al, bh, idesc, 1);
+                    }
+            } else {
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t bh = tc::smem_desc(tc.bsm + 256 * ks, 128, sbo);
+                    const uint64_t bl = tc::smem_desc(tc.bsm + tc.bbytes + 256 * ks, 128, sbo);
+                    const uint32_t ah = A + 8 * ks, al = ah + 32;
+                    tc::mma_f16_ts(D, ah, bh, idesc, ks);
+                    tc::mma_f16_ts(D, ah, bl, idesc, 1);
+                    tc::mma_f16_ts(D, al, bh, idesc, 1);
                 }
             }
-        } else {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            mma3(d, fa[0], bh[0][0], bh[0][1], bl[0][0], bl[0][1]);
-            mma3(d, fa[1], bh[1][0], bh[1][1], bl[1][0], bl[1][1]);
-            const int so = bd + vd * half;   // output half o = vd
-            Sc[sw(so, gg)] = make_float2(d[0], d[1]);
-            Sc[sw(so, gg + 8)] = make_float2(d[2], d[3]);
+        }
+        tc::mma_commit(tc.mbar);
+    }
+    if (!*tc.fail && !tc::mbar_wait(tc.mbar, tc.phase)) {
+        *tc.fail = 1;
+        atomicExch(&g_tc_wait_timeout, 1);
+    }
+    tc.phase ^= 1u;
+    tc::fence_after();
+    float2 y[R];
+    if (MS) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) y[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            // D_e columns (2 i' + re/im): i' < 8 in d0, i' >= 8 in d1;  h[o][e][i] = D_e[o ? i : R - 1 - i]
+            uint32_t d0[16], d1[16];
+            tc::tmem_ld16(tcol + 64 + 32 * e, d0);
+            tc::tmem_ld16(tcol + 80 + 32 * e, d1);
+            tc::tmem_wait_ld();
+            const float4* re = e ? r1 : r0;
+#pragma unroll
+            for (int m = 0; m < R / 2; ++m) {
+                const float4 pq = re[m ^ sw8];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = 2 * m + u, ii = R - 1 - i;
+                    const float2 hf = i < 8 ? make_float2(__uint_as_float(d0[2 * i]), __uint_as_float(d0[2 * i + 1]))
+                                            : make_float2(__uint_as_float(d1[2 * i - 16]), __uint_as_float(d1[2 * i - 15]));
+                    const float2 hr = ii < 8 ? make_float2(__uint_as_float(d0[2 * ii]), __uint_as_float(d0[2 * ii + 1]))
+                                             : make_float2(__uint_as_float(d1[2 * ii - 16]), __uint_as_float(d1[2 * ii - 15]));
+                    const float2 h = cscale(o ? hf : hr, isc);
+                    const float2 f = u ? make_float2(pq.z, pq.w) : make_float2(pq.x, pq.y);
+                    if (!ADJ) cfma(y[i], f, h);
+                    else cfmac(y[i], f, h);
+                }
+            }
+        }
+    } else {
+        uint32_t d0[16], d1[16];
+        tc::tmem_ld16(tcol + 64, d0);
+        tc::tmem_ld16(tcol + 80, d1);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < R / 2; ++j) {
+            y[j] = make_float2(__uint_as_float(d0[2 * j]) * isc, __uint_as_float(d0[2 * j + 1]) * isc);
+            y[j + R / 2] = make_float2(__uint_as_float(d1[2 * j]) * isc, __uint_as_float(d1[2 * j + 1]) * isc);
         }
     }
+    store_pair(Sc, o ? base + half : base, y);
+    tc::fence_before();
+}
+
+// CTA set-up of the tensor-core levels: TMEM (warp 0), mbarrier, B operands.
+template <bool MS, bool BF>
+__device__ void tc_setup(Tc& tc, unsigned char* bsmem, const float* sPc, uint32_t* s_tmem, uint64_t* s_mbar, int* s_fail) {
+    if (threadIdx.x < 32) tc::tmem_alloc(s_tmem, kTmemCols);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(s_mbar, 1);
+        *s_fail = 0;
+    }
+    build_b<MS, BF>(bsmem, sPc);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    tc.tmem = *s_tmem;
+    tc.mbar = s_mbar;
+    tc.fail = s_fail;
+    tc.phase = 0;
+    tc.bsm = tc::smem_addr(bsmem);
+    tc.bbytes = MS ? kBBytesMS : kBBytesSM;
+}
+__device__ __forceinline__ void tc_teardown(const Tc& tc) {
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x < 32) tc::tmem_free(tc.tmem, kTmemCols);
 }
 
 // One chunk of M (forward, RIGHT) or M^* (adjoint, LEFT), in place: task =
@@ -834,7 +973,7 @@ __device__ void pipeline3(int nitem, int P, float4* buf0, float4* buf1, StageF s
     }
 }
 
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
     Geo g;
@@ -846,11 +985,16 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     float4* buf1 = buf0 + P * 16;
     float* sPc = reinterpret_cast<float*>(buf0 + nbuf3(P) * P * 16);
     float* sPU = sPc + 2 * PCS;
+    unsigned char* bsm = tc_bsm(sPU + kLeafMax * RS);
     const int lsU = 1 << (g.L - g.sU), nbU = lsU;
     const int kc = min(KC, a.k - col0);
     const int nlev = g.sU - g.h;
     const int nitem = nlev + (ADJ ? 8 : 0);
-    SplitFrag fa[2];
+    constexpr bool TC = MODE != kSimt;
+    __shared__ uint32_t s_tmem;
+    __shared__ uint64_t s_mbar;
+    __shared__ int s_fail;
+    Tc tc;
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
@@ -862,9 +1006,9 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
-            if (SPLIT) {
-                if (ADJ) level3_tc<true, false, true>(S, fa, cur, s, g);
-                else level3_tc<true, true, false>(S, fa, cur, s, g);
+            if (TC) {   // adjoint B^* levels scale then mix, forward B levels mix then scale
+                if (ADJ) level3_tc<true, false, true, MODE == kTcBF16>(S, cur, s, g, tc);
+                else level3_tc<true, true, false, MODE == kTcBF16>(S, cur, s, g, tc);
             } else {
                 if (ADJ) level3<true, false, true>(S, sPc, cur, s, g);
                 else level3<true, true, false>(S, sPc, cur, s, g);
@@ -880,15 +1024,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[(e / R) * RS + e % R] = a.P[a.pu_off + e];
     __syncthreads();
-    // split-precision A fragments: forward B levels are mix-then-scale (P_o), adjoint B^* scale-then-mix (P_e^T)
-    if (SPLIT) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float* Pm = sPc + c * PCS;
-            fa[c] = !ADJ ? afrag([&](int r_, int c_) { return Pm[r_ * R + c_]; })
-                         : afrag([&](int r_, int c_) { return Pm[c_ * R + r_]; });
-        }
-    }
+    if (TC && nlev > 0) tc_setup<!ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, &s_mbar, &s_fail);
     const int nB = nlev, lo = g.L - g.sU;
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U^*
@@ -961,9 +1097,10 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
         }
     }
+    if (TC && nlev > 0) tc_teardown(tc);
 }
 
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
     Geo g;
@@ -975,12 +1112,17 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     float4* buf1 = buf0 + P * 16;
     float* sPc = reinterpret_cast<float*>(buf0 + nbuf3(P) * P * 16);
     float* sPV = sPc + 2 * PCS;
+    unsigned char* bsm = tc_bsm(sPV + kLeafMax * RS);
     const int lsV = 1 << g.sV, na = 1 << g.sV, nl = 1 << (g.h - g.sV);
     const int kc = min(KC, a.k - col0);
     const int64_t nmid = int64_t(1) << (g.L - g.h);
     const int nlev = g.h - g.sV;
     const int nitem = nlev + (ADJ ? 0 : 8);
-    SplitFrag fa[2];
+    constexpr bool TC = MODE != kSimt;
+    __shared__ uint32_t s_tmem;
+    __shared__ uint64_t s_mbar;
+    __shared__ int s_fail;
+    Tc tc;
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
@@ -992,9 +1134,9 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
-            if (SPLIT) {
-                if (ADJ) level3_tc<false, true, true>(S, fa, cur, s, g);
-                else level3_tc<false, false, false>(S, fa, cur, s, g);
+            if (TC) {   // adjoint C^* levels mix then scale, forward C levels scale then mix
+                if (ADJ) level3_tc<false, true, true, MODE == kTcBF16>(S, cur, s, g, tc);
+                else level3_tc<false, false, false, MODE == kTcBF16>(S, cur, s, g, tc);
             } else {
                 if (ADJ) level3<false, true, true>(S, sPc, cur, s, g);
                 else level3<false, false, false>(S, sPc, cur, s, g);
@@ -1010,15 +1152,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[(e / R) * RS + e % R] = a.P[e];
     __syncthreads();
-    // split-precision A fragments: adjoint C^* levels are mix-then-scale (P_o), forward C scale-then-mix (P_e^T)
-    if (SPLIT) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float* Pm = sPc + c * PCS;
-            fa[c] = ADJ ? afrag([&](int r_, int c_) { return Pm[r_ * R + c_]; })
-                        : afrag([&](int r_, int c_) { return Pm[c_ * R + r_]; });
-        }
-    }
+    if (TC && nlev > 0) tc_setup<ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, &s_mbar, &s_fail);
     if (ADJ) {
         for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
             const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
@@ -1089,41 +1223,50 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i] = S[col * P * R + sw(lp, i)];
         }
     }
+    if (TC && nlev > 0) tc_teardown(tc);
 }
 
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_left3(HalfArgs a) {
-    left3_body<ADJ, SPLIT>(a, blockIdx.y, blockIdx.x * (NT >> (a.L - a.h)));
+    left3_body<ADJ, MODE>(a, blockIdx.y, blockIdx.x * (NT >> (a.L - a.h)));
 }
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_right3(HalfArgs a) {
-    right3_body<ADJ, SPLIT>(a, blockIdx.y, blockIdx.x * (NT >> a.h));
+    right3_body<ADJ, MODE>(a, blockIdx.y, blockIdx.x * (NT >> a.h));
 }
 
 // Grouped launch over several operators: CTA b runs item items[b] =
 // (operator, box, first column) of the operators' half passes.
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_left3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
     const int4 it = items[blockIdx.x];
-    left3_body<ADJ, SPLIT>(args[it.x], it.y, it.z);
+    left3_body<ADJ, MODE>(args[it.x], it.y, it.z);
 }
-template <bool ADJ, bool SPLIT>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_right3_group(const HalfArgs* __restrict__ args, const int4* __restrict__ items) {
     const int4 it = items[blockIdx.x];
-    right3_body<ADJ, SPLIT>(args[it.x], it.y, it.z);
+    right3_body<ADJ, MODE>(args[it.x], it.y, it.z);
 }
 
+// Dynamic shared memory: state (64 KiB), one or two table buffers of P * 256 B, Lagrange
+// tables, and (aligned to 128 B) the B operands of the tensor-core levels.  Tensor-core
+// launches ask for at least kSmemTcMin so that one CTA -- which holds all 512 TMEM
+// columns -- is resident per SM.
+constexpr size_t kSmemB = 2 * kBBytesSM + 128;
 inline size_t smem3(int P) {
-    return size_t(NT) * R * 8 + size_t(P <= 256 ? 2 : 1) * P * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float);
+    return size_t(NT) * R * 8 + size_t(P <= 256 ? 2 : 1) * P * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float) + kSmemB;
 }
-constexpr size_t kSmem3Max = size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float);
+constexpr size_t kSmem3Max =
+    size_t(NT) * R * 8 + size_t(2) * 256 * 256 + (2 * PCS + kLeafMax * RS) * sizeof(float) + kSmemB;
+constexpr size_t kSmemTcMin = 120 * 1024;
+inline size_t smem3_launch(int P, int mode) { return mode == kSimt ? smem3(P) : std::max(smem3(P), kSmemTcMin); }
 
-template <bool SPLIT> cudaError_t set_attrs3_t() {
+template <int MODE> cudaError_t set_attrs3_t() {
     const int mx = int(kSmem3Max);
-    const void* fns[] = {(const void*)k_left3<true, SPLIT>,        (const void*)k_left3<false, SPLIT>,
-                         (const void*)k_right3<true, SPLIT>,       (const void*)k_right3<false, SPLIT>,
-                         (const void*)k_left3_group<true, SPLIT>,  (const void*)k_left3_group<false, SPLIT>,
-                         (const void*)k_right3_group<true, SPLIT>, (const void*)k_right3_group<false, SPLIT>};
+    const void* fns[] = {(const void*)k_left3<true, MODE>,        (const void*)k_left3<false, MODE>,
+                         (const void*)k_right3<true, MODE>,       (const void*)k_right3<false, MODE>,
+                         (const void*)k_left3_group<true, MODE>,  (const void*)k_left3_group<false, MODE>,
+                         (const void*)k_right3_group<true, MODE>, (const void*)k_right3_group<false, MODE>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
@@ -1133,8 +1276,9 @@ template <bool SPLIT> cudaError_t set_attrs3_t() {
 inline fio_status set_attrs3() {
     static PerDeviceOnce attrs;
     FIO_CUDA(attrs.run([] {
-        const cudaError_t e = set_attrs3_t<false>();
-        return e == cudaSuccess ? set_attrs3_t<true>() : e;
+        cudaError_t e = set_attrs3_t<kSimt>();
+        if (e == cudaSuccess) e = set_attrs3_t<kTcF16>();
+        return e == cudaSuccess ? set_attrs3_t<kTcBF16>() : e;
     }));
     return FIO_OK;
 }
@@ -1145,8 +1289,10 @@ fio_status left3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t st
     const int P = 1 << (bf->L - bf->h), KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << bf->h);
     const char* nm = ADJ ? "k_bf_left_adj" : "k_bf_left_fwd";
-    if (a.split) FIO_LAUNCH(nm, st, k_left3<ADJ, true><<<g, NT, smem3(P), st>>>(a));
-    else FIO_LAUNCH(nm, st, k_left3<ADJ, false><<<g, NT, smem3(P), st>>>(a));
+    const size_t sm = smem3_launch(P, a.mode);
+    if (a.mode == kTcF16) FIO_LAUNCH(nm, st, k_left3<ADJ, kTcF16><<<g, NT, sm, st>>>(a));
+    else if (a.mode == kTcBF16) FIO_LAUNCH(nm, st, k_left3<ADJ, kTcBF16><<<g, NT, sm, st>>>(a));
+    else FIO_LAUNCH(nm, st, k_left3<ADJ, kSimt><<<g, NT, sm, st>>>(a));
     return FIO_OK;
 }
 template <bool ADJ>
@@ -1155,8 +1301,10 @@ fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t s
     const int P = 1 << bf->h, KC = NT / P;
     dim3 g((kcols + KC - 1) / KC, 1 << (bf->L - bf->h));
     const char* nm = ADJ ? "k_bf_right_adj" : "k_bf_right_fwd";
-    if (a.split) FIO_LAUNCH(nm, st, k_right3<ADJ, true><<<g, NT, smem3(P), st>>>(a));
-    else FIO_LAUNCH(nm, st, k_right3<ADJ, false><<<g, NT, smem3(P), st>>>(a));
+    const size_t sm = smem3_launch(P, a.mode);
+    if (a.mode == kTcF16) FIO_LAUNCH(nm, st, k_right3<ADJ, kTcF16><<<g, NT, sm, st>>>(a));
+    else if (a.mode == kTcBF16) FIO_LAUNCH(nm, st, k_right3<ADJ, kTcBF16><<<g, NT, sm, st>>>(a));
+    else FIO_LAUNCH(nm, st, k_right3<ADJ, kSimt><<<g, NT, sm, st>>>(a));
     return FIO_OK;
 }
 
@@ -1190,7 +1338,7 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
         a.sU = bf->sU;
         a.sV = bf->sV;
         a.k = ops[o].k;
-        a.split = bf->split ? 1 : 0;
+        a.mode = bf_fused_mode(bf, -1);
         HalfArgs al = a, ar = a;
         for (size_t i = 0; i < bf->B.size() && i < 24; ++i) al.tab.t[i] = bf->B[i].as<float2>();
         for (size_t i = 0; i < bf->C.size() && i < 24; ++i) ar.tab.t[i] = bf->C[i].as<float2>();
@@ -1215,35 +1363,69 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
 
 size_t bf_group_args_size() { return sizeof(HalfArgs); }
 
-// Launch the two grouped halves (device copies of the tables of bf_group_tables).
+// Launch the two grouped halves (device copies of the tables of bf_group_tables); `mode`
+// is the transfer-level mode shared by every operator of the launch (bf_fused_mode).
 fio_status bf_group_launch(const void* dleft_args, const int4* dleft_items, int nleft, const void* dright_args,
-                           const int4* dright_items, int nright, int adjoint, int split, cudaStream_t st) {
+                           const int4* dright_items, int nright, int adjoint, int mode, cudaStream_t st) {
     FIO_TRY(v3::set_attrs3());
     const HalfArgs* la = static_cast<const HalfArgs*>(dleft_args);
     const HalfArgs* ra = static_cast<const HalfArgs*>(dright_args);
     const size_t sm = v3::kSmem3Max;
     const int NT = v3::NT;
+    auto left = [&](auto kern, const char* nm) -> fio_status {
+        if (nleft) FIO_LAUNCH(nm, st, kern<<<nleft, NT, sm, st>>>(la, dleft_items));
+        return FIO_OK;
+    };
+    auto right = [&](auto kern, const char* nm) -> fio_status {
+        if (nright) FIO_LAUNCH(nm, st, kern<<<nright, NT, sm, st>>>(ra, dright_items));
+        return FIO_OK;
+    };
+    using namespace v3;
     if (adjoint) {
-        if (nleft) {
-            if (split) FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true, true><<<nleft, NT, sm, st>>>(la, dleft_items));
-            else FIO_LAUNCH("k_bf_left_adj_group", st, v3::k_left3_group<true, false><<<nleft, NT, sm, st>>>(la, dleft_items));
-        }
-        if (nright) {
-            if (split) FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true, true><<<nright, NT, sm, st>>>(ra, dright_items));
-            else FIO_LAUNCH("k_bf_right_adj_group", st, v3::k_right3_group<true, false><<<nright, NT, sm, st>>>(ra, dright_items));
+        if (mode == kTcF16) {
+            FIO_TRY(left(k_left3_group<true, kTcF16>, "k_bf_left_adj_group"));
+            FIO_TRY(right(k_right3_group<true, kTcF16>, "k_bf_right_adj_group"));
+        } else if (mode == kTcBF16) {
+            FIO_TRY(left(k_left3_group<true, kTcBF16>, "k_bf_left_adj_group"));
+            FIO_TRY(right(k_right3_group<true, kTcBF16>, "k_bf_right_adj_group"));
+        } else {
+            FIO_TRY(left(k_left3_group<true, kSimt>, "k_bf_left_adj_group"));
+            FIO_TRY(right(k_right3_group<true, kSimt>, "k_bf_right_adj_group"));
         }
     } else {
-        if (nright) {
-            if (split) FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false, true><<<nright, NT, sm, st>>>(ra, dright_items));
-            else FIO_LAUNCH("k_bf_right_fwd_group", st, v3::k_right3_group<false, false><<<nright, NT, sm, st>>>(ra, dright_items));
-        }
-        if (nleft) {
-            if (split) FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false, true><<<nleft, NT, sm, st>>>(la, dleft_items));
-            else FIO_LAUNCH("k_bf_left_fwd_group", st, v3::k_left3_group<false, false><<<nleft, NT, sm, st>>>(la, dleft_items));
+        if (mode == kTcF16) {
+            FIO_TRY(right(k_right3_group<false, kTcF16>, "k_bf_right_fwd_group"));
+            FIO_TRY(left(k_left3_group<false, kTcF16>, "k_bf_left_fwd_group"));
+        } else if (mode == kTcBF16) {
+            FIO_TRY(right(k_right3_group<false, kTcBF16>, "k_bf_right_fwd_group"));
+            FIO_TRY(left(k_left3_group<false, kTcBF16>, "k_bf_left_fwd_group"));
+        } else {
+            FIO_TRY(right(k_right3_group<false, kSimt>, "k_bf_right_fwd_group"));
+            FIO_TRY(left(k_left3_group<false, kSimt>, "k_bf_left_fwd_group"));
         }
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
+}
+
+// Transfer-level mode of the staged fused kernels for this handle: split precision ->
+// BF16 parts on the tensor cores; the FP32 setting -> FP16 parts on the tensor cores,
+// or CUDA-core FP32 when the handle asks for it.  prec: -1 the handle's precision,
+// 0 FP32, 1 split BF16.
+int bf_fused_mode(const fio_bf* bf, int prec) {
+    const bool split = prec < 0 ? bf->split : prec == 1;
+    if (split) return v3::kTcBF16;
+    return bf->simt ? v3::kSimt : v3::kTcF16;
+}
+
+int tc_wait_timeouts() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, v3::g_tc_wait_timeout, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(v3::g_tc_wait_timeout, &z, sizeof(int));
+    }
+    return v;
 }
 
 bool bf_v3_ok(const fio_bf* bf) {
@@ -1264,7 +1446,7 @@ int bf_fused_kc(const fio_bf* bf) {
 }
 
 fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kcols, int adjoint,
-                          float2* mid, cudaStream_t st) {
+                          float2* mid, cudaStream_t st, int prec) {
     HalfArgs a;
     a.X = X;
     a.ldx = ld;
@@ -1283,12 +1465,12 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
     a.sU = bf->sU;
     a.sV = bf->sV;
     a.k = kcols;
-    a.split = bf->split ? 1 : 0;
+    a.mode = bf_fused_mode(bf, prec);
     // the left kernels read E tables (B levels), the right kernels F tables (C levels)
     Tabs tl{}, tr{};
     for (size_t i = 0; i < bf->B.size() && i < 24; ++i) tl.t[i] = bf->B[i].as<float2>();
     for (size_t i = 0; i < bf->C.size() && i < 24; ++i) tr.t[i] = bf->C[i].as<float2>();
-    if (bf_v3_ok(bf) && (!bf->fused_v2 || bf->split)) {
+    if (bf_v3_ok(bf) && (!bf->fused_v2 || a.mode == v3::kTcBF16)) {
         HalfArgs al = a, ar = a;
         al.tab = tl;
         ar.tab = tr;

@@ -26,8 +26,8 @@ __global__ void k_add(float2* __restrict__ f, const float2* __restrict__ d, int6
 
 using namespace fio;
 
-extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, void* F, int64_t ld, int k, int refine_steps,
-                                void* stream) {
+extern "C" fio_status fio_solve(const fio_bf* bf, const fio_hss* hc, const void* U, void* F, int64_t ld, int k,
+                                int refine_steps, void* stream) {
     if (!bf || !hc) return fail(FIO_EINVAL, "fio_solve: null handle");
     if (bf->N() != hc->N) return fail(FIO_EINVAL, "fio_solve: BF and HSS sizes differ");
     if (k < 0 || ld < hc->N || refine_steps < 0) return fail(FIO_EINVAL, "fio_solve: bad k, ld or refine_steps");
@@ -53,25 +53,23 @@ extern "C" fio_status fio_solve(fio_bf* bf, const fio_hss* hc, const void* U, vo
     if (refine_steps > 0) {
         float2* R1 = T + ld * k;
         float2* R2 = R1 + ld * k;
-        // residuals of Eq. 4.3 against the FP32 applies of K~ and K~^*
-        const bool was_split = bf->split;
-        bf->split = false;
+        // residuals of Eq. 4.3 against the FP32 applies of K~ and K~^* (precision request 0;
+        // the handle's own setting is left as it is)
         float2* T32 = T;
         fio_status s = FIO_OK;
         if (split_refine) {
             T32 = R2 + ld * k;
-            s = bf_apply_ord(bf, Uc, T32, ld, k, 1, mort, st);
+            s = bf_apply_ord(bf, Uc, T32, ld, k, 1, mort, st, 0);
         }
         dim3 g(cdiv(N, 256), k);
         for (int it = 0; it < refine_steps && s == FIO_OK; ++it) {
-            s = bf_apply_ord(bf, static_cast<const float2*>(F), R1, ld, k, 0, mort, st);   // K~ f
-            if (s == FIO_OK) s = bf_apply_ord(bf, R1, R2, ld, k, 1, mort, st);             // K~^* K~ f
+            s = bf_apply_ord(bf, static_cast<const float2*>(F), R1, ld, k, 0, mort, st, 0);   // K~ f
+            if (s == FIO_OK) s = bf_apply_ord(bf, R1, R2, ld, k, 1, mort, st, 0);             // K~^* K~ f
             if (s != FIO_OK) break;
             FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T32, R2, R1, N, ld, ld, ld));
             s = hss_solve(h, R1, R2, ld, k, st);
             if (s == FIO_OK) FIO_LAUNCH("k_add", st, k_add<<<g, 256, 0, st>>>(static_cast<float2*>(F), R2, N, ld, ld));
         }
-        bf->split = was_split;
         FIO_TRY(s);
     }
     if (mort) FIO_TRY(bf2d_unmorton(bf, static_cast<const float2*>(F), Fout, ld, k, st));

@@ -111,7 +111,10 @@ def test_bf_apply_full_size_sampled_rows_and_dft():
 
 @pytest.mark.parametrize("n", [1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18])
 def test_fused_equals_per_level(n):
-    """The two kernel paths agree to FP32 rounding at every size of the batched/serving workloads."""
+    """The kernel paths agree at every size of the batched/serving workloads: the CUDA-core paths
+    (per-level, fused_v2, fused_simt) to FP32 rounding (2e-6), the staged fused path with its
+    tensor-core transfer levels (FP16 hi + lo parts, 22 significand bits, FP32 accumulation)
+    to 5e-6."""
     from paper_2609_11520_b300 import BF
     gb = BF(n, 16)
     X = to_dev(crandn(n, 5, seed=n % 977))
@@ -119,8 +122,10 @@ def test_fused_equals_per_level(n):
         a = to_np(gb.set_path("fused").apply(X, adjoint=adj))
         b = to_np(gb.set_path("per_level").apply(X, adjoint=adj))
         c = to_np(gb.set_path("fused_v2").apply(X, adjoint=adj))
-        assert rel(a, b) < 2e-6
+        d = to_np(gb.set_path("fused_simt").apply(X, adjoint=adj))
+        assert rel(a, b) < 5e-6
         assert rel(c, b) < 2e-6
+        assert rel(d, b) < 2e-6
 
 
 def test_bf_set_path_rejects_unsupported():
