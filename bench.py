@@ -163,9 +163,9 @@ def kernel_fma(name, N, r, kc, binfo):
     return None
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak of a B300: 148 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
-    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, sm_count):
+    """FP32 FMA peak: SMs (from the device) x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def parse_profile(text):
@@ -176,39 +176,62 @@ def parse_profile(text):
     return out
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernel build
-# (profiles/k_left3_bf_adjoint_N65536_k64.md): kernel name, N, columns per launch, precision.
-NCU_TRAFFIC = {("k_bf_left_adj", 1 << 16, 64, "fp32"): 256216320 + 490535680}
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernel build:
+# (kernel name, N, columns per launch, transfer-level arithmetic) -> bytes, or absent.
+NCU_TRAFFIC = {}
 
 
-def roofline_entry(name, per_launch_ms, nbytes, nfma, hbm_peak, peak_src, clocks, traffic=None):
-    """Roofline of the dominant kernel.  Fused BF half passes are FP32-ALU bound at wide k (their DRAM
-    bytes equal the algorithmic bytes, profiles/k_bf_fused_*), so they report FP32 FLOP/s against
-    the FP32 FMA peak at the maximum SM clock; other kernels report HBM bytes."""
+def roofline_entry(name, per_launch_ms, nbytes, nfma, hbm_peak, peak_src, clocks, sm_count, traffic=None):
+    """Roofline of the dominant kernel against the measured HBM copy bandwidth.  The fused BF half
+    passes move their transfer-level products to the tensor cores, so their ideal time is set by
+    the algorithmic HBM bytes; the FP32-FMA equivalent of their arithmetic (what the CUDA-core
+    variant issues) is reported beside it for context."""
     hbm_achieved = nbytes / (per_launch_ms / 1e3) / 1e9 if nbytes else None
+    out = {"kernel": name, "bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+           "bytes_per_launch": nbytes, "ms_per_launch": per_launch_ms, "traffic": traffic}
     if nfma:
         sm_max = clocks.get("sm_max_mhz") or 2032.0
-        peak = fp32_peak_tflops(sm_max)
-        achieved = 2 * nfma / (per_launch_ms / 1e3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 x %.0f MHz" % sm_max,
-                "flops_per_launch": 2 * nfma, "bytes_per_launch": nbytes,
-                "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,
-                "traffic": traffic}
-    return {"kernel": name, "bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src,
-            "bytes_per_launch": nbytes, "traffic": traffic}
+        fp = fp32_peak_tflops(sm_max, sm_count)
+        out["fp32_equivalent"] = {"tflops": 2 * nfma / (per_launch_ms / 1e3) / 1e12, "peak_tflops": fp,
+                                  "peak_source": "derived: %d SMs (device attribute) x 128 FP32 FMA/clk x 2 x %.0f MHz"
+                                                 % (sm_count, sm_max)}
+    return out
 
 
-def cpu_oracle_online(n, steps, warmup, leaf, r, rank_per_level=8, seed=3):
-    """Oracle online stage, one RHS per step: K~^* u (factor blocks built first) + ULV solve."""
+def operator_ranks(n, leaf):
+    """Per-level HSS ranks of the oracle's own construction of the N = 2^16 operator (stored by
+    tests/golden/make_solve_golden.py, which calls only oracle/); None if absent or another size."""
+    path = os.path.join(ROOT, "tests", "golden", "solve1d_N65536.txt")
+    if n != 1 << 16 or leaf != 128 or not os.path.exists(path):
+        return None
+    vals = dict(line.split(maxsplit=1) for line in open(path) if not line.startswith("#"))
+    return [int(v) for v in vals["ranks"].split()]
+
+
+def cpu_oracle_online(n, steps, warmup, leaf, r, seed=3, threads=None):
+    """Oracle online stage, one RHS per step: K~^* u (factor blocks built first) + ULV solve on an
+    HSS with the tree and per-level ranks of the operator's own (oracle-built) HSS.  The solve's
+    cost depends only on that shape, so its generators are random (building the oracle's HSS at
+    N = 2^16 takes about 20 minutes).  threads: BLAS threads; a number runs the measurement in a
+    child process whose BLAS libraries start with that many threads (None = this process, all
+    cores)."""
+    if threads is not None:
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+                   MKL_NUM_THREADS=str(threads))
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle", str(steps), str(warmup),
+                              str(threads)], capture_output=True, text=True, env=env, cwd=ROOT)
+        if out.returncode != 0:
+            raise RuntimeError("CPU oracle child failed: " + out.stderr[-2000:])
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+        return d["value"], threads, d["sample"], d["times"]
     from oracle.butterfly import Butterfly1D
     from oracle.hss import ULV, random_hss
     from oracle.problem import Phase
     cores = len(os.sched_getaffinity(0))
-    bf = Butterfly1D(Phase("cabs"), n, r, cache=True)
     Lh = int(np.log2(n // leaf))
-    ranks = [0] + [rank_per_level] * Lh
+    ranks = operator_ranks(n, leaf) or ([0] + [8] * Lh)
+    bf = Butterfly1D(Phase("cabs"), n, r, cache=True)
     hss = random_hss(n, leaf, ranks, np.random.default_rng(0), shift=float(n))
     ulv = ULV(hss)
     u = crandn(n, 1, seed)
@@ -223,10 +246,11 @@ def cpu_oracle_online(n, steps, warmup, leaf, r, rank_per_level=8, seed=3):
         if i >= warmup:
             times.append(dt)
     med = statistics.median(times)
-    sample = (f"{steps} RHS of the N=2^16 workload, one per step (median {med:.2f} s): oracle K~^* apply "
-              f"(complex128, factor blocks built once beforehand in {setup:.1f} s, excluded) + oracle ULV "
-              f"solve on an HSS of the same tree (leaf {leaf}, {Lh} levels, rank {rank_per_level} per level)")
-    return 1.0 / med, cores, sample, times
+    used = int(os.environ.get("OPENBLAS_NUM_THREADS", cores))
+    sample = (f"{steps} RHS of the N=2^16 workload, one per step (median {med:.2f} s, {used} BLAS threads): "
+              f"oracle K~^* apply (complex128, factor blocks built once beforehand in {setup:.1f} s, excluded) + "
+              f"oracle ULV solve on an HSS with the operator's tree and ranks {ranks}")
+    return 1.0 / med, used, sample, times
 
 
 def run_reference(args):
@@ -356,15 +380,16 @@ def run_2d(args):
     print(json.dumps(line))
 
 
-def run_batched(args):
-    """Batched workload: 32 operators, N uniform over 2^12..2^17, 16 RHS each, one step = all 512 RHS."""
+def batched_leg(steps, warmup, count=32):
+    """Config-4 workload: `count` operators, N uniform over 2^12..2^17 (seed 4), s ~ U[0.5, 1], 16 RHS
+    each; one step = one solve of every operator's block.  Times every mode of fio_batch_* after the
+    autotuner and returns the summary dict."""
     import torch
     from fio_inputs import batched_operators
     from paper_2609_11520_b300 import BF, HSS, Batch
-    torch.cuda.set_device(0)
     t0 = time.perf_counter()
     ops = []
-    for i, (n, sdepth) in enumerate(batched_operators()):
+    for i, (n, sdepth) in enumerate(batched_operators(count)):
         bf = BF(n, 16, "cabs", sdepth)
         ops.append((bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=40 + i).factor()))
     t_build = time.perf_counter() - t0
@@ -377,46 +402,50 @@ def run_batched(args):
     times = {}
     for mode in ("per_operator", "grouped", "graph"):
         b.set_mode(mode)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             b.solve(Us, Fs)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.solve(Us, Fs)
         ev[1].record()
         ev[1].synchronize()
-        times[mode] = ev[0].elapsed_time(ev[1]) / args.steps
+        times[mode] = ev[0].elapsed_time(ev[1]) / steps
     best = min(times, key=times.get)
     nrhs = k * len(ops)
-    line = {"metric": "RHS solves/s, batched workload (32 uneven 1D operators x 16 RHS)", "value": nrhs / (times[best] / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": times[best],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "batched1d: 32 operators, N uniform over {2^12..2^17} (seed 4), s ~ U[0.5, 1], "
-                                   "BF r 16, HSS leaf 128 tol 1e-3, 16 RHS each", "offline_build_s": round(t_build, 2),
-                       "ms_per_step_by_mode": times, "mode": best, "autotune": report.strip().splitlines()}}
-    print(json.dumps(line))
+    return {"rhs_per_s": nrhs / (times[best] / 1e3), "ms_per_step": times[best], "mode": best,
+            "ms_per_step_by_mode": {m: round(v, 4) for m, v in times.items()}, "operators": len(ops),
+            "rhs_per_step": nrhs, "offline_build_s": round(t_build, 2),
+            "autotune": report.strip().splitlines(),
+            "workload": "32 1D operators, N uniform over {2^12..2^17} (seed 4), s ~ U[0.5, 1], BF r 16, "
+                        "HSS leaf 128 tol 1e-3, 16 RHS each, device-resident inputs"}
 
 
-def run_serving(args):
-    """Serving workload: resident operators, Poisson arrivals, 1..32 RHS per request, p50 / p99."""
+SERVING_1D = [(1 << 14, 1.0), (1 << 15, 1.0), (1 << 16, 1.0), (1 << 16, 0.5), (1 << 17, 1.0), (1 << 18, 1.0)]
+
+
+def serving_leg(nreq, rates=(0.5, 0.8, 1.0), ops2d=(64,), seed=5):
+    """Config-5 workload through the continuous-batching server: resident operators (the six 1D
+    operators of SERVING_1D and 2D elliptic operators with n per dimension in ops2d), Poisson
+    arrivals (seed 5) at the given fractions of the measured saturated request rate, 1..32 RHS per
+    request from pinned host memory (H2D and D2H inside each request's latency)."""
     import torch
     from fio_inputs import poisson_requests
     from paper_2609_11520_b300 import BF, HSS
     from paper_2609_11520_b300.serve import Server, latency_stats
-    torch.cuda.set_device(0)
-    specs = [(1 << 14, 1.0), (1 << 15, 1.0), (1 << 16, 1.0), (1 << 16, 0.5), (1 << 17, 1.0), (1 << 18, 1.0)]
+    t0 = time.perf_counter()
     ops = {}
-    for i, (n, sdepth) in enumerate(specs):
+    for i, (n, sdepth) in enumerate(SERVING_1D):
         bf = BF(n, 16, "cabs", sdepth)
-        ops[f"n{n}_s{sdepth}"] = (bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=70 + i).factor())
+        ops[f"1d_n{n}_s{sdepth}"] = (bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=70 + i).factor())
+    for i, n2 in enumerate(ops2d):
+        bf = BF(n2, 25, "elliptic2d")
+        ops[f"2d_n{n2}"] = (bf, HSS.from_samples(bf=bf, leaf=256, oversample=10, tol=1e-3, seed=90 + i).factor())
+    t_build = time.perf_counter() - t0
     names = sorted(ops)
-    nreq = args.requests
-
-    # Request inputs are slices of one pinned pool of 64 random columns per operator, and
-    # solutions land in a pinned output pool per operator (a request's columns are
-    # delivered there; later requests of that operator overwrite them), so the trace
-    # holds ~0.3 GB of host memory instead of one fresh buffer per request.
+    # request inputs: slices of a pinned pool of 64 random columns per operator; solutions land in a
+    # pinned output pool per operator
     rng = np.random.default_rng(6)
     pool_in, pool_out = {}, {}
     for nm in names:
@@ -425,33 +454,52 @@ def run_serving(args):
         pool_in[nm] = torch.from_numpy(u).pin_memory()
         pool_out[nm] = torch.empty_like(pool_in[nm]).pin_memory()
 
-    def trace(rate, seed):
-        t, oi, ks = poisson_requests(nreq, rate, len(names), seed=seed, kmax=32)
-        offs = np.random.default_rng(seed + 1).integers(0, 33, size=len(t))
-        out = []
-        for ti, o, kk, off in zip(t, oi, ks, offs):
-            nm = names[o]
-            out.append((float(ti), nm, pool_in[nm][off:off + kk], pool_out[nm][off:off + kk]))
-        return out
+    def trace(rate, sd):
+        t, oi, ks = poisson_requests(nreq, rate, len(names), seed=sd, kmax=32)
+        offs = np.random.default_rng(sd + 1).integers(0, 33, size=len(t))
+        return [(float(ti), names[o], pool_in[names[o]][off:off + kk], pool_out[names[o]][off:off + kk])
+                for ti, o, kk, off in zip(t, oi, ks, offs)]
 
-    # saturated throughput: every request arrives at t = 0
-    sat_trace = [(0.0,) + tuple(x[1:]) for x in trace(1.0, 5)]
-    Server(ops, kmax=64, n_slots=4).run(sat_trace[: min(200, nreq)])   # warm-up
+    sat_trace = [(0.0,) + tuple(x[1:]) for x in trace(1.0, seed)]
+    Server(ops, kmax=64, n_slots=4).run(sat_trace[: min(100, nreq)])   # warm-up
     sat = latency_stats(Server(ops, kmax=64, n_slots=4).run(sat_trace))
-    avg_k = np.mean([x[2].shape[0] for x in sat_trace])
+    avg_k = float(np.mean([x[2].shape[0] for x in sat_trace]))
     req_rate = sat["rhs_per_s"] / avg_k
-    rates = {}
-    for frac in (0.5, 0.8, 1.0):
-        st = latency_stats(Server(ops, kmax=64, n_slots=4).run(trace(frac * req_rate, 5)))
-        rates[str(frac)] = {k_: round(v, 4) if isinstance(v, float) else v for k_, v in st.items()}
+    by_rate = {}
+    for frac in rates:
+        st = latency_stats(Server(ops, kmax=64, n_slots=4).run(trace(frac * req_rate, seed)))
+        by_rate[str(frac)] = {k_: round(v, 4) if isinstance(v, float) else v for k_, v in st.items()}
+    top = by_rate[str(max(rates))]
+    return {"p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "rhs_per_s": sat["rhs_per_s"],
+            "requests_per_rate": nreq, "saturated": {k_: round(v, 4) if isinstance(v, float) else v for k_, v in sat.items()},
+            "by_rate_fraction": by_rate, "offline_build_s": round(t_build, 2), "operators": names,
+            "workload": "continuous batching over resident operators (1D N = 2^14, 2^15, 2^16, 2^16 with s = 0.5, "
+                        "2^17, 2^18; 2D elliptic n = %s), Poisson arrivals (seed 5), 1..32 RHS per request, kmax 64, "
+                        "4 streams, pinned host requests (H2D and D2H inside the latency); p50/p99 at the highest "
+                        "rate fraction, rhs_per_s saturated" % ", ".join(str(x) for x in ops2d)}
+
+
+def run_batched(args):
+    """Batched workload alone (one JSON line)."""
+    import torch
+    torch.cuda.set_device(0)
+    b = batched_leg(args.steps, args.warmup)
+    line = {"metric": "RHS solves/s, batched workload (32 uneven 1D operators x 16 RHS)", "value": b["rhs_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batched1d: " + b["workload"]}, "batched": b}
+    print(json.dumps(line))
+
+
+def run_serving(args):
+    """Serving workload alone (one JSON line), with the 2D operators of --serve-2d."""
+    import torch
+    torch.cuda.set_device(0)
+    sv = serving_leg(args.requests, ops2d=tuple(int(x) for x in args.serve_2d.split(",") if x))
     line = {"metric": "RHS solves/s served (continuous batching, Poisson arrivals); p50/p99 latency",
-            "value": sat["rhs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": nreq, "warmup": min(200, nreq),
+            "value": sv["rhs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.requests, "warmup": 100,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-            "data": "synthetic",
-            "config": {"workload": "serving: 6 resident 1D operators (N = 2^14, 2^15, 2^16, 2^16 with s = 0.5, 2^17, "
-                                   "2^18), Poisson arrivals (seed 5), 1..32 RHS per request, kmax 64, 4 streams, "
-                                   "host-resident requests (H2D and D2H inside the latency)",
-                       "requests": nreq, "saturated": sat, "by_rate_fraction": rates}}
+            "data": "synthetic", "config": {"workload": "serving: " + sv["workload"]}, "served_requests": sv}
     print(json.dumps(line))
 
 
@@ -504,6 +552,11 @@ def run_profile_case(args):
 
 
 def main():
+    if len(sys.argv) == 5 and sys.argv[1] == "--cpu-oracle":   # child of cpu_oracle_online(threads=...)
+        w = WORKLOADS["large1d"]
+        v, _, sample, times = cpu_oracle_online(w["n"], int(sys.argv[2]), int(sys.argv[3]), w["leaf"], w["r"])
+        print(json.dumps({"value": v, "sample": sample, "times": times}))
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -513,6 +566,9 @@ def main():
     ap.add_argument("--workload", default="large1d", choices=["large1d", "batched1d", "serving", "2d"])
     ap.add_argument("--n2d", type=int, default=64)
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--serve-2d", default="64", help="n per dimension of the 2D serving operators, comma separated")
+    ap.add_argument("--serve-requests", type=int, default=600, help="requests per rate of the default line's serving leg")
+    ap.add_argument("--no-legs", action="store_true", help="skip the serving and batched legs of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     choices=["bf_adjoint", "bf_forward", "hss_solve", "fio_solve", "bf2d_adjoint", "bf2d_forward"])
@@ -609,18 +665,51 @@ def main():
     plain = timed(lambda: fio_solve(bf, hss, U1, out=O1), args.steps, args.warmup)
     plain_value = 1e3 / statistics.mean(plain)
 
-    # ---- end to end through the public API with pinned host buffers ----
-    Uh = U.cpu().pin_memory()
-    Oh = torch.empty(Uh.shape, dtype=Uh.dtype).pin_memory()
-    Ud = torch.empty_like(U)
+    # ---- end to end through the public API with pinned host buffers: every step copies its block of
+    # right-hand sides host->device and its solutions device->host; steps are pipelined over two
+    # buffers, an H2D stream and a D2H stream, so the copies of step i+1 and i-1 overlap the solve
+    # of step i ----
+    Uh = [U.cpu().pin_memory() for _ in range(2)]
+    Oh = [torch.empty(U.shape, dtype=U.dtype).pin_memory() for _ in range(2)]
+    Ud = [torch.empty_like(U) for _ in range(2)]
+    Od = [torch.empty_like(U) for _ in range(2)]
+    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    solved = [torch.cuda.Event() for _ in range(2)]
+    d2h_done = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        Ud.copy_(Uh, non_blocking=True)
-        fio_solve(bf, hss, Ud, out=OUT)
-        Oh.copy_(OUT, non_blocking=True)
+    def e2e_run(nsteps):
+        for i in range(nsteps):
+            j = i & 1
+            with torch.cuda.stream(h2d_s):
+                h2d_s.wait_event(solved[j])              # the solve that last read Ud[j] is done
+                Ud[j].copy_(Uh[j], non_blocking=True)
+                h2d_done[j].record(h2d_s)
+            stream.wait_event(h2d_done[j])
+            stream.wait_event(d2h_done[j])               # Od[j] has been copied out
+            fio_solve(bf, hss, Ud[j], out=Od[j], stream=stream)
+            solved[j].record(stream)
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(solved[j])
+                Oh[j].copy_(Od[j], non_blocking=True)
+                d2h_done[j].record(d2h_s)
 
-    e2e = timed(e2e_step, args.steps, args.warmup)
-    e2e_value = world * k * args.steps / (sum(e2e) / 1e3)
+    for j in range(2):
+        solved[j].record(stream)
+        d2h_done[j].record(d2h_s)
+    e2e_run(args.warmup)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    h2d_s.wait_event(ea)
+    d2h_s.wait_event(ea)
+    e2e_run(args.steps)
+    stream.wait_stream(d2h_s)
+    eb.record(stream)
+    eb.synchronize()
+    e2e_ms = ea.elapsed_time(eb)
+    e2e_value = world * k * args.steps / (e2e_ms / 1e3)
+    e2e_err = float(torch.linalg.norm(Oh[(args.steps - 1) & 1].cuda() - F_true) / torch.linalg.norm(F_true))
 
     # ---- per-kernel CUDA-event attribution over an identical pass ----
     _lib.lib.fio_profile_enable(1)
@@ -638,10 +727,14 @@ def main():
     peak, peak_src = load_peaks()
     per_launch_ms = top[1][1] / top[1][0]
     nbytes = kernel_bytes(top[0], n, r, kc, binfo, hinfo)
-    achieved = nbytes / (per_launch_ms / 1e3) / 1e9 if nbytes else None
     nfma = kernel_fma(top[0], n, r, kc, binfo)
     kernels = {name: {"launches": c, "ms_total": round(ms, 4), "share": round(ms / sum(v[1] for v in prof.values()), 4)}
                for name, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- the same block with the FP32 transfer levels on the CUDA cores instead of the tensor cores ----
+    bf.set_path("fused_simt")
+    simt = timed(lambda: fio_solve(bf, hss, U, out=OUT), args.steps, args.warmup)
+    bf.set_path("auto")
 
     # ---- split-precision transfer levels (BF16 hi + lo on the tensor cores), same served block ----
     split = None
@@ -661,12 +754,33 @@ def main():
                  "refine1": {"value": world * k * args.steps / (sum(sp1) / 1e3), "e_vs_f_true": e_sp1},
                  "fp32_refine1": {"value": world * k * args.steps / (sum(fp1) / 1e3), "e_vs_f_true": e_fp1}}
 
+    # ---- preconditioned CG on Eq. 4.3 (Section 4.1), same block, tolerance 1e-5 ----
+    from paper_2609_11520_b300 import fio_pcg
+    pcg_info = {}
+
+    def pcg_step():
+        _, it, rr = fio_pcg(bf, hss, U, out=OUT, tol=1e-5, maxit=30)
+        pcg_info.update(iterations=it, max_relres=max(rr))
+
+    pcg_t = timed(pcg_step, max(3, args.steps // 4), 1)
+    pcg = {"value": world * k * len(pcg_t) / (sum(pcg_t) / 1e3), "unit": UNIT, "tol": 1e-5,
+           "e_vs_f_true": float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true)), **pcg_info}
+
+    legs = {}
+    if rank == 0 and world == 1 and not args.no_legs:
+        legs["served_requests"] = serving_leg(args.serve_requests,
+                                              ops2d=tuple(int(x) for x in args.serve_2d.split(",") if x))
+        legs["batched"] = batched_leg(max(3, args.steps // 2), args.warmup)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cv, cores, sample, _ = cpu_oracle_online(n, 3, 0, w["leaf"], r)
-        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cv1, _, sample1, _ = cpu_oracle_online(n, 2, 0, w["leaf"], r, threads=1)
+        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "one_thread": {"value": cv1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
     if rank == 0:
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(served), "higher_is_better": True,
@@ -678,20 +792,26 @@ def main():
                 "offline_s": {"bf_build": round(t_bf, 3), "hss_build": round(t_hss, 3), "ulv_factor": round(t_fac, 3)},
                 "hss_ranks": hinfo["ranks"], "hss_samples": hinfo["samples"],
                 "e_direct_vs_f_true": e_direct, "parallelism": f"replicas x{world}",
+                "transfer_levels": "tcgen05 tensor cores, FP16 hi/lo three-term products (FP32 accuracy)",
             },
             "latency_ms": {"served_p50": percentile(served, 50), "served_p99": percentile(served, 99),
                            "plain_p50": percentile(plain, 50), "plain_p99": percentile(plain, 99)},
             "plain": {"value": plain_value, "unit": UNIT, "k_per_call": 1},
+            "cuda_core_fp32": {"value": world * k * args.steps / (sum(simt) / 1e3), "unit": UNIT,
+                               "ms_per_step": statistics.mean(simt)},
             "split_bf16": split,
+            "pcg": pcg,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(U.numel() * 8),
-                    "d2h_bytes_per_step": int(U.numel() * 8)},
+                    "d2h_bytes_per_step": int(U.numel() * 8), "e_vs_f_true": e2e_err,
+                    "pipelining": "two buffers; H2D and D2H on their own streams overlap the neighbouring steps' solves"},
             "gpu_launches": int(launches),
             "kernels": kernels,
-            "roofline": roofline_entry(top[0], per_launch_ms, nbytes, nfma, peak, peak_src, clk.summary(),
-                                       NCU_TRAFFIC.get((top[0], n, kc, "fp32"))),
+            "roofline": roofline_entry(top[0], per_launch_ms, nbytes, nfma, peak, peak_src, clk.summary(), sm_count,
+                                       NCU_TRAFFIC.get((top[0], n, kc, "tc_f16"))),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
+        line.update(legs)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -30,6 +30,13 @@ def crandn(n, k, seed):
     return rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
 
 
+def bump_centers(N, m=10, seed=7):
+    """(m, 2) centres (x_k, xi_k) of the Gaussian-bump amplitude of Section 5.1: x_k ~ U[0, 1],
+    xi_k ~ U[-N/2, N/2] (the paper draws them at random without giving the draw)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.0, 1.0, m), rng.uniform(-N / 2, N / 2, m)], axis=1)
+
+
 def batched_operators(count=32, seed=4, logs=(12, 13, 14, 15, 16, 17)):
     """(N, s) per operator: N uniform over 2^logs, s ~ U[0.5, 1]."""
     rng = np.random.default_rng(seed)

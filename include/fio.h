@@ -50,15 +50,37 @@ typedef enum {
 typedef enum {
     FIO_PHASE_DFT = 0,        /* Phi = x . xi, d = 1 or 2  (then K^* K = N I exactly) */
     FIO_PHASE_1D_CABS = 1,    /* d = 1: Phi = x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/16 */
-    FIO_PHASE_2D_ELLIPTIC = 2 /* d = 2: Phi = x . xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
+    FIO_PHASE_2D_ELLIPTIC = 2,/* d = 2: Phi = x . xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
                                  c1 = (2 + sin 2 pi x1 sin 2 pi x2)/16,
                                  c2 = (2 + cos 2 pi x1 cos 2 pi x2)/16 (Section 5.2) */
+    FIO_PHASE_1D_CABS8 = 3,   /* d = 1: Phi = x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/8
+                                 (the operator of Section 5.1) */
+    FIO_PHASE_2D_ISO = 4      /* d = 2: Phi = x . xi + c(x) ||xi||,
+                                 c(x) = (3 + s sin 2 pi x1 sin 2 pi x2)/8 (Section 5.3) */
 } fio_phase_kind;
 
 typedef struct {
     int kind;     /* fio_phase_kind */
     double s;     /* modulation depth s of c(x); 1.0 for the standard operator */
 } fio_phase;
+
+/* Amplitude a(x, xi) of Eq. 1.2 (a = 1 unless given).  It enters only the
+ * middle factor of the BF, M = a(z, gamma) e^{2 pi i Phi(z, gamma)} (Section
+ * 2.2), so it must be smooth on the Chebyshev grids of the middle level. */
+typedef enum {
+    FIO_AMP_ONE = 0,     /* a = 1 */
+    FIO_AMP_BUMPS = 1,   /* d = 1 (Section 5.1): a = sum_k exp(-((x - x_k)^2 + ((xi - xi_k)/N)^2) / sigma2) */
+    FIO_AMP_HANKEL = 2   /* d = 2 with FIO_PHASE_2D_ISO (Section 5.3): a = H0^(1)(2 pi phi) e^{-2 pi i phi},
+                            phi = Phi - x . xi = c(x) ||xi|| (infinite at xi = 0, which no Chebyshev
+                            point of the middle level reaches) */
+} fio_amp_kind;
+#define FIO_AMP_MAX_BUMPS 32
+typedef struct {
+    int kind;               /* fio_amp_kind */
+    int m;                  /* FIO_AMP_BUMPS: number of bumps, 1 .. FIO_AMP_MAX_BUMPS */
+    double sigma2;          /* FIO_AMP_BUMPS: sigma^2 > 0 */
+    const double* centers;  /* FIO_AMP_BUMPS: host array of m pairs (x_k, xi_k), read during the call */
+} fio_amp;
 
 typedef struct fio_bf fio_bf;
 typedef struct fio_hss fio_hss;
@@ -94,6 +116,16 @@ typedef struct {
  *   Errors: FIO_EINVAL (sizes), FIO_ENOMEM, FIO_ECUDA.
  * ---------------------------------------------------------------------- */
 fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, fio_bf** out);
+
+/* bf_build_amp -- bf_build with an amplitude (the paper's bf_build(phase, amp,
+ *   n, d, r)); amp = NULL is a = 1.  Only the middle factor changes: its
+ *   entries are multiplied by a(z_i, gamma_j), evaluated in FP64 on the device
+ *   (the Bessel functions J0, Y0 of the Hankel amplitude by CUDA's j0, y0).
+ *   Errors: FIO_EINVAL for an amplitude the dimension or phase does not admit
+ *   (bumps: d = 1; Hankel: d = 2 with FIO_PHASE_2D_ISO), m out of range or
+ *   sigma2 <= 0; otherwise as bf_build. */
+fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, void* stream,
+                        fio_bf** out);
 
 /* bf_apply -- Y = K~ X (adjoint = 0) or Y = K~^* X (adjoint = 1); the adjoint
  *   applies the conjugate-transposed factors in reverse order (Section 2.2).
@@ -216,6 +248,23 @@ fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int
 fio_status fio_solve(const fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k,
                      int refine_steps, void* stream);
 
+/* fio_pcg -- the iterative use of Algorithm 1's output (Section 4.1): conjugate
+ *   gradients on the approximate normal equation K~^* K~ f = K~^* u (Eq. 4.3),
+ *   preconditioned by the ULV factorization F~ = G~^{-1} of the HSS.  Each
+ *   column is its own CG run from f_0 = 0; a column stops when its recurrence
+ *   residual satisfies ||r|| <= tol ||K~^* u|| (the paper's stopping rule with
+ *   tol = 1e-12 in FP64; the complex64 applies here floor the attainable
+ *   relative residual near 1e-6, so useful tolerances are >= 1e-6), or after
+ *   maxit iterations.  Inner products and CG scalars are FP64 on the device.
+ *   U, F: device, N x k complex64, ld >= N, no overlap (2D: lexicographic
+ *   order, the iteration runs in the HSS's quadtree order).  iters (host, may
+ *   be NULL): iterations taken by the slowest column; relres (host, k
+ *   doubles, may be NULL): final relative residual per column.  The HSS must
+ *   be factored (hss_ulv_factor).  Synchronizes `stream` once per iteration
+ *   (convergence test on the host).  Errors: FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA. */
+fio_status fio_pcg(const fio_bf* bf, const fio_hss* hss, const void* U, void* F, int64_t ld, int k, double tol,
+                   int maxit, int* iters, double* relres, void* stream);
+
 /* fio_set_large_node -- node-size threshold of the large-node kernels (no
  *   paper counterpart; process-wide, default 384).  HSS levels with at most 16
  *   nodes of size m >= m_min (the top levels of 2D operators, whose ranks grow
@@ -234,6 +283,10 @@ fio_status fio_solve(const fio_bf* bf, const fio_hss* hss, const void* U, void* 
  *   by a few.
  *   Errors: FIO_EINVAL for m_min < 1. */
 fio_status fio_set_large_node(int m_min);
+
+/* fio_set_large_node_count -- the large-node kernels take levels with at most
+ *   max_nodes nodes (process-wide, default 16); FIO_EINVAL for max_nodes < 1. */
+fio_status fio_set_large_node_count(int max_nodes);
 
 void hss_free(fio_hss* hss);
 

@@ -67,9 +67,12 @@ def lagrange(nodes, x):
 
 
 class Butterfly1D:
-    """BF of the 1D FIO with amplitude 1 (Eq. 2.1), applied block by block."""
+    """BF of the 1D FIO (Eq. 2.1), applied block by block.  The amplitude (default a = 1) enters
+    only the middle factor, M = k(z_i, gamma_j) = a(z_i, gamma_j) e^{2 pi i Phi(z_i, gamma_j)}
+    (Section 2.2); the interpolation factors are amplitude-free."""
 
-    def __init__(self, phase, n, r, max_block_elems=1 << 23, cache=None, levels=None):
+    def __init__(self, phase, n, r, max_block_elems=1 << 23, cache=None, levels=None, amp=None):
+        self.amp = amp
         L = int(round(np.log2(n)))
         if 2 ** L != n or L < 2:
             raise ValueError("n must be a power of two >= 4")
@@ -156,12 +159,13 @@ class Butterfly1D:
         return np.exp(TWO_PI_I * ph) * np.transpose(qv, (0, 3, 1, 2))[None]
 
     def M_block(self, a):
-        """M[a, b, i, j] = e^{2 pi i Phi(z_a_i, gamma_b_j)} at the middle level h."""
+        """M[a, b, i, j] = a(z_a_i, gamma_b_j) e^{2 pi i Phi(z_a_i, gamma_b_j)} at the middle level h."""
         L, h = self.L, self.h
         b = np.arange(2 ** (L - h))
         z = self.space_nodes(h, a)[:, None, :, None]
         gam = self.freq_nodes(L - h, b)[None, :, None, :]
-        return np.exp(TWO_PI_I * self.phase(z, gam))
+        m = np.exp(TWO_PI_I * self.phase(z, gam))
+        return m if self.amp is None else self.amp(z, gam) * m
 
     def B_block(self, s, a_out):
         """Block [a', b', i, beta, t] of B (pair level s -> s+1), a' at level s+1."""

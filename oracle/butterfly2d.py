@@ -46,9 +46,11 @@ def _tensor_lagrange(n1, n2, p1, p2):
 
 
 class Butterfly2D:
-    """BF of the 2D FIO with amplitude 1, r = r1^2 tensor Chebyshev nodes per box."""
+    """BF of the 2D FIO, r = r1^2 tensor Chebyshev nodes per box; the amplitude (default a = 1)
+    enters only the middle factor M (Section 2.2)."""
 
-    def __init__(self, phase, n, r1, max_block_elems=1 << 23, levels=None):
+    def __init__(self, phase, n, r1, max_block_elems=1 << 23, levels=None, amp=None):
+        self.amp = amp
         L = int(round(np.log2(n)))
         if 2 ** L != n or L < 2:
             raise ValueError("n must be a power of two >= 4")
@@ -171,12 +173,13 @@ class Butterfly2D:
         return np.exp(TWO_PI_I * ph) * np.transpose(qv, (0, 3, 1, 2))[None]
 
     def M_block(self, a):
-        """[a, b, i, j] = e^{2 pi i Phi(z_a_i, gamma_b_j)} at the middle level h."""
+        """[a, b, i, j] = a(z_a_i, gamma_b_j) e^{2 pi i Phi(z_a_i, gamma_b_j)} at the middle level h."""
         L, h = self.L, self.h
         b = np.arange(4 ** (L - h))
         z = self.space_nodes(h, a)[:, None, :, None, :]
         gam = self.freq_nodes(L - h, b)[None, :, None, :, :]
-        return np.exp(TWO_PI_I * self.phase(z, gam))
+        m = np.exp(TWO_PI_I * self.phase(z, gam))
+        return m if self.amp is None else self.amp(z, gam) * m
 
     def B_block(self, s, a_out):
         """[a', b', i, c, t] of B (pair level s -> s+1): a' at space level s+1 with

@@ -14,8 +14,8 @@ from .hss import ULV, build_blackbox
 
 
 class FIOSolver:
-    def __init__(self, phase, n, r, leaf, p, tol, seed, rank_frac=0.5):
-        self.bf = Butterfly1D(phase, n, r)
+    def __init__(self, phase, n, r, leaf, p, tol, seed, rank_frac=0.5, amp=None):
+        self.bf = Butterfly1D(phase, n, r, amp=amp)
         self.stats = {}
         self.hss = build_blackbox(lambda X: self.bf.adjoint(self.bf.apply(X)),
                                   n, leaf, p, tol, seed, rank_frac=rank_frac, stats=self.stats)
@@ -32,10 +32,10 @@ class FIOSolver2D:
     quadtree boxes and their concatenations (a binary tree whose levels
     alternate the split direction); f^ = P^T F~ P K~^* u."""
 
-    def __init__(self, phase, n, r1, leaf, p, tol, seed, rank_frac=0.5):
+    def __init__(self, phase, n, r1, leaf, p, tol, seed, rank_frac=0.5, amp=None):
         from .butterfly2d import Butterfly2D
         from .problem import morton_order
-        self.bf = Butterfly2D(phase, n, r1)
+        self.bf = Butterfly2D(phase, n, r1, amp=amp)
         self.perm = morton_order(n)
         self.stats = {}
         N = n * n

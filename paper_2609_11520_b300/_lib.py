@@ -12,7 +12,8 @@ LIB_PATH = os.path.join(HERE, "libfio_b300.so")
 FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ENOTHPD, FIO_ERANK, FIO_ETIMEOUT, FIO_EBUSY = range(8)
 STATUS_NAMES = ["FIO_OK", "FIO_EINVAL", "FIO_ENOMEM", "FIO_ECUDA", "FIO_ENOTHPD", "FIO_ERANK",
                 "FIO_ETIMEOUT", "FIO_EBUSY"]
-PHASE_KINDS = {"dft": 0, "cabs": 1, "elliptic2d": 2}
+PHASE_KINDS = {"dft": 0, "cabs": 1, "elliptic2d": 2, "cabs8": 3, "iso2d": 4}
+AMP_KINDS = {"one": 0, "bumps": 1, "hankel": 2}
 SAMPLER_NORMAL, SAMPLER_DENSE = 0, 1
 
 
@@ -25,6 +26,11 @@ class FioError(RuntimeError):
 
 class Phase(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("s", ctypes.c_double)]
+
+
+class Amp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("m", ctypes.c_int), ("sigma2", ctypes.c_double),
+                ("centers", ctypes.POINTER(ctypes.c_double))]
 
 
 class Sampler(ctypes.Structure):
@@ -40,6 +46,7 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = {
     "bf_build": (I32, [ctypes.POINTER(Phase), I32, I32, I32, P, PP]),
     "bf_apply": (I32, [P, P, P, I64, I32, I32, P]),
+    "bf_build_amp": (I32, [ctypes.POINTER(Phase), ctypes.POINTER(Amp), I32, I32, I32, P, PP]),
     "bf_info": (I32, [P, ctypes.POINTER(I64)]),
     "bf_set_path": (I32, [P, I32]),
     "bf_set_precision": (I32, [P, I32]),
@@ -62,8 +69,11 @@ SIGNATURES = {
     "fio_batch_free": (None, [P]),
     "fio_last_error": (ctypes.c_char_p, []),
     "fio_device_status": (I32, []),
+    "fio_pcg": (I32, [P, P, P, P, I64, I32, ctypes.c_double, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double),
+                      P]),
     "fio_profile_enable": (I32, [I32]),
     "fio_set_large_node": (I32, [I32]),
+    "fio_set_large_node_count": (I32, [I32]),
     "fio_profile_report": (I32, [ctypes.c_char_p, I64]),
 }
 

@@ -12,7 +12,7 @@ import torch
 from . import _lib
 from ._lib import FioError, check, lib
 
-__all__ = ["BF", "HSS", "Batch", "fio_solve", "device_status", "FioError"]
+__all__ = ["BF", "HSS", "Batch", "fio_solve", "fio_pcg", "device_status", "FioError"]
 
 
 def _stream(stream=None):
@@ -41,11 +41,26 @@ class BF:
     and are held as (k, N) complex64 CUDA tensors; `self.n` is N.
     """
 
-    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None, d=None):
-        d = (2 if phase == "elliptic2d" else 1) if d is None else int(d)
+    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None, d=None, amp=None):
+        """amp: None (a = 1), ("bumps", centers, sigma2) with centers an (m, 2) array of (x_k, xi_k)
+        (Section 5.1), or "hankel" (Section 5.3, with phase "iso2d")."""
+        d = (2 if phase in ("elliptic2d", "iso2d") else 1) if d is None else int(d)
         ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
         h = ctypes.c_void_p()
-        check(lib.bf_build(ctypes.byref(ph), int(n), d, int(r), _stream(stream), ctypes.byref(h)))
+        if amp is None:
+            check(lib.bf_build(ctypes.byref(ph), int(n), d, int(r), _stream(stream), ctypes.byref(h)))
+        else:
+            import numpy as np
+            kind = amp if isinstance(amp, str) else amp[0]
+            a = _lib.Amp(_lib.AMP_KINDS[kind], 0, 1.0, None)
+            keep = None
+            if kind == "bumps":
+                keep = np.ascontiguousarray(np.asarray(amp[1], dtype=np.float64).reshape(-1, 2))
+                a.m, a.sigma2 = keep.shape[0], float(amp[2])
+                a.centers = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            check(lib.bf_build_amp(ctypes.byref(ph), ctypes.byref(a), int(n), d, int(r), _stream(stream),
+                                   ctypes.byref(h)))
+            del keep
         self._h = h
         self.n_side, self.d = int(n), d
         self.n, self.r, self.phase, self.s = int(n) ** d, int(r), phase, float(s)
@@ -189,6 +204,19 @@ def fio_solve(bf, hss, U, out=None, refine_steps=0, stream=None):
     check(lib.fio_solve(bf.handle, hss.handle, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k,
                         int(refine_steps), _stream(stream)))
     return out
+
+
+def fio_pcg(bf, hss, U, out=None, tol=1e-6, maxit=50, stream=None):
+    """CG on K~^* K~ f = K~^* u preconditioned by the ULV factorization of G~ (Section 4.1).
+    Returns (F, iterations, relative residual per column)."""
+    px, ld, k = _block(U, bf.n, "U")
+    out = torch.empty_like(U) if out is None else out
+    py, _, _ = _block(out, bf.n, "F")
+    it = ctypes.c_int(0)
+    rr = (ctypes.c_double * max(k, 1))()
+    check(lib.fio_pcg(bf.handle, hss.handle, ctypes.c_void_p(px), ctypes.c_void_p(py), ld, k, float(tol), int(maxit),
+                      ctypes.byref(it), rr, _stream(stream)))
+    return out, int(it.value), [float(rr[i]) for i in range(k)]
 
 
 class Batch:

@@ -22,6 +22,18 @@ struct Cheb {
 __device__ __forceinline__ double phi(const PhaseDev& p, double x, double xi) {
     double v = x * xi;
     if (p.kind == FIO_PHASE_1D_CABS) v += (2.0 + p.s * sinpi(2.0 * x)) * 0.0625 * fabs(xi);
+    if (p.kind == FIO_PHASE_1D_CABS8) v += (2.0 + p.s * sinpi(2.0 * x)) * 0.125 * fabs(xi);
+    return v;
+}
+
+// a(x, xi) of the 1D amplitudes (Gaussian bumps of Section 5.1, or 1).
+__device__ __forceinline__ double amp1d(const AmpDev& a, double x, double xi) {
+    if (a.kind != FIO_AMP_BUMPS) return 1.0;
+    double v = 0.0;
+    for (int k = 0; k < a.m; ++k) {
+        const double dx = x - a.c[2 * k], dxi = (xi - a.c[2 * k + 1]) / a.N;
+        v += exp(-(dx * dx + dxi * dxi) / a.sigma2);
+    }
     return v;
 }
 
@@ -100,8 +112,9 @@ __global__ void k_tab_E(float2* E, PhaseDev ph, Cheb ch, int n, int L, int s, in
     E[e] = expi2pi(phi(ph, z, freq_center(n, L - s, 2 * bq + be)) - phi(ph, z, freq_center(n, L - s - 1, bq)));
 }
 
-// M[p][i][j], pair p = tau * 2^(L-h) + sigma at the middle level h.
-__global__ void k_tab_M(float2* M, PhaseDev ph, Cheb ch, int n, int L, int h, int r) {
+// M[p][i][j], pair p = tau * 2^(L-h) + sigma at the middle level h; the amplitude
+// a(z_i, gamma_j) multiplies the entry (it enters no other factor).
+__global__ void k_tab_M(float2* M, PhaseDev ph, AmpDev amp, Cheb ch, int n, int L, int h, int r) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= int64_t(n) * r * r) return;
     int j = int(e % r), i = int((e / r) % r);
@@ -110,7 +123,8 @@ __global__ void k_tab_M(float2* M, PhaseDev ph, Cheb ch, int n, int L, int h, in
     int64_t tau = p / nb, sg = p % nb;
     double z = space_node(ch, h, tau, i), y = space_center(h, tau);
     double g = freq_node(ch, n, L - h, sg, j), eta = freq_center(n, L - h, sg);
-    M[e] = expi2pi(phi(ph, z, g) - phi(ph, z, eta) - phi(ph, y, g));
+    const float2 m = expi2pi(phi(ph, z, g) - phi(ph, z, eta) - phi(ph, y, g));
+    M[e] = amp.kind == FIO_AMP_ONE ? m : cscale(m, float(amp1d(amp, z, g)));
 }
 
 // ---------------------------------------------------------------- apply
@@ -387,15 +401,40 @@ fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t l
 using namespace fio;
 
 extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, fio_bf** out) {
+    return bf_build_amp(phase, nullptr, n, d, r, stream, out);
+}
+
+extern "C" fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, void* stream,
+                                   fio_bf** out) {
     if (!out || !phase) return fail(FIO_EINVAL, "bf_build: null pointer");
     *out = nullptr;
+    AmpDev ad;
+    if (amp && amp->kind != FIO_AMP_ONE) {
+        if (amp->kind == FIO_AMP_BUMPS) {
+            if (d != 1) return fail(FIO_EINVAL, "bf_build_amp: the Gaussian-bump amplitude is 1D");
+            if (amp->m < 1 || amp->m > FIO_AMP_MAX_BUMPS || !amp->centers || !(amp->sigma2 > 0.0))
+                return fail(FIO_EINVAL, "bf_build_amp: bumps need 1 <= m <= FIO_AMP_MAX_BUMPS, centers and sigma2 > 0");
+            ad.kind = FIO_AMP_BUMPS;
+            ad.m = amp->m;
+            ad.sigma2 = amp->sigma2;
+            ad.N = double(n);
+            for (int k = 0; k < 2 * amp->m; ++k) ad.c[k] = amp->centers[k];
+        } else if (amp->kind == FIO_AMP_HANKEL) {
+            if (d != 2 || phase->kind != FIO_PHASE_2D_ISO)
+                return fail(FIO_EINVAL, "bf_build_amp: the Hankel amplitude needs d = 2 and FIO_PHASE_2D_ISO");
+            ad.kind = FIO_AMP_HANKEL;
+        } else {
+            return fail(FIO_EINVAL, "bf_build_amp: unknown amplitude kind");
+        }
+    }
     if (d == 2) {
         const int L2 = ilog2_exact(n);
         if (L2 < 3 || L2 > 10) return fail(FIO_EINVAL, "bf_build: 2D needs n a power of two in [8, 1024]");
         if (r != 25) return fail(FIO_EINVAL, "bf_build: 2D needs r = 25 (5 x 5 tensor Chebyshev grid)");
-        if (!bf2d_ok_kind(phase->kind)) return fail(FIO_EINVAL, "bf_build: 2D phase must be DFT or 2D elliptic");
+        if (!bf2d_ok_kind(phase->kind)) return fail(FIO_EINVAL, "bf_build: 2D phase must be DFT, 2D elliptic or 2D iso");
         fio_bf* bf = new fio_bf();
         bf->phase = *phase;
+        bf->amp = ad;
         bf->nside = n; bf->n = n * n; bf->d = 2; bf->r = r; bf->L = L2;
         bf->h = L2 / 2;
         bf->sU = std::max(L2 - 3, bf->h);
@@ -409,15 +448,17 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
         return FIO_OK;
     }
     if (d != 1) return fail(FIO_EINVAL, "bf_build: d must be 1 or 2");
-    if (phase->kind == FIO_PHASE_2D_ELLIPTIC) return fail(FIO_EINVAL, "bf_build: the elliptic phase is 2D (d = 2)");
+    if (phase->kind == FIO_PHASE_2D_ELLIPTIC || phase->kind == FIO_PHASE_2D_ISO)
+        return fail(FIO_EINVAL, "bf_build: that phase is 2D (d = 2)");
     int L = ilog2_exact(n);
     if (L < 4 || L > 24) return fail(FIO_EINVAL, "bf_build: n must be a power of two in [16, 2^24]");
     if (r < 1 || r > kMaxR) return fail(FIO_EINVAL, "bf_build: r must be in [1, 16]");
-    if (phase->kind != FIO_PHASE_DFT && phase->kind != FIO_PHASE_1D_CABS)
+    if (phase->kind != FIO_PHASE_DFT && phase->kind != FIO_PHASE_1D_CABS && phase->kind != FIO_PHASE_1D_CABS8)
         return fail(FIO_EINVAL, "bf_build: unknown phase kind");
     cudaStream_t st = as_stream(stream);
     fio_bf* bf = new fio_bf();
     bf->phase = *phase;
+    bf->amp = ad;
     bf->n = n; bf->nside = n; bf->d = d; bf->r = r; bf->L = L;
     bf->h = L / 2;
     bf->sU = std::max(L - 3, bf->h);
@@ -451,7 +492,7 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
     if ((s = bf->M.ensure(nM * 8)) != FIO_OK) return cleanup(s);
     k_tab_VP<<<cdiv(nVP, TB), TB, 0, st>>>(bf->VP.as<float2>(), ph, n, bf->sV);
     k_tab_UP<<<cdiv(nUP, TB), TB, 0, st>>>(bf->UP.as<float2>(), ph, n, L, bf->sU);
-    k_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), ph, ch, n, L, bf->h, r);
+    k_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), ph, bf->amp, ch, n, L, bf->h, r);
     bf->C.resize(bf->h - bf->sV);
     for (int lv = bf->sV; lv < bf->h; ++lv) {
         if ((s = bf->C[lv - bf->sV].ensure(nT * 8)) != FIO_OK) return cleanup(s);

@@ -24,8 +24,18 @@
 #pragma once
 #include "common.cuh"
 
+// Amplitude of the middle factor, by value in kernel parameters.
+struct AmpDev {
+    int kind = FIO_AMP_ONE;
+    int m = 0;
+    double sigma2 = 1.0;
+    double N = 1.0;                          // vector length (bumps scale xi by 1/N)
+    double c[2 * FIO_AMP_MAX_BUMPS] = {};    // (x_k, xi_k)
+};
+
 struct fio_bf {
     fio_phase phase;
+    AmpDev amp;
     int n = 0, d = 1, r = 0, L = 0, h = 0, sU = 0, sV = 0;   // n: vector length N (n^d)
     int nside = 0;                 // points per dimension; L = log2 nside
     int lsV = 0, lsU = 0;          // points per V frequency leaf / per U space leaf

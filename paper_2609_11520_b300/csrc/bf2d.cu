@@ -45,15 +45,33 @@ struct Cheb5 {
     double t[R1];
 };
 
-// Phi(x, xi) of the 2D families (Section 5.2; Phi = x . xi for the DFT).
-__device__ __forceinline__ double phi2(int kind, double x1, double x2, double k1, double k2) {
-    double v = x1 * k1 + x2 * k2;
+// Nonlinear part Phi(x, xi) - x . xi of the 2D families (Sections 5.2 and 5.3; 0 for the DFT).
+__device__ __forceinline__ double phi2_nl(int kind, double s, double x1, double x2, double k1, double k2) {
     if (kind == FIO_PHASE_2D_ELLIPTIC) {
         const double c1 = (2.0 + sinpi(2.0 * x1) * sinpi(2.0 * x2)) * 0.0625;
         const double c2 = (2.0 + cospi(2.0 * x1) * cospi(2.0 * x2)) * 0.0625;
-        v += sqrt(c1 * c1 * k1 * k1 + c2 * c2 * k2 * k2);
+        return sqrt(c1 * c1 * k1 * k1 + c2 * c2 * k2 * k2);
     }
-    return v;
+    if (kind == FIO_PHASE_2D_ISO) return (3.0 + s * sinpi(2.0 * x1) * sinpi(2.0 * x2)) * 0.125 * sqrt(k1 * k1 + k2 * k2);
+    return 0.0;
+}
+// The handle's 2D phase (kind and modulation depth s), by value in kernel parameters.
+struct Ph2 {
+    int kind;
+    double s;
+};
+// Phi(x, xi) of the 2D families.
+__device__ __forceinline__ double phi2(const Ph2& p, double x1, double x2, double k1, double k2) {
+    return x1 * k1 + x2 * k2 + phi2_nl(p.kind, p.s, x1, x2, k1, k2);
+}
+
+// Hankel amplitude of Section 5.3: a = H0^(1)(2 pi phi) e^{-2 pi i phi}, H0^(1) = J0 + i Y0.
+__device__ __forceinline__ float2 hankel_amp(double ph) {
+    const double z = 2.0 * M_PI * ph;
+    const double jr = j0(z), yi = y0(z);
+    double sn, cs;
+    sincospi(2.0 * ph, &sn, &cs);
+    return make_float2(float(jr * cs + yi * sn), float(yi * cs - jr * sn));
 }
 
 // e^{2 pi i ph}: reduce modulo 1 in FP64, then sin/cos of the remainder.
@@ -95,7 +113,7 @@ __device__ __forceinline__ int64_t fidx(int j1, int j2, int n, int L, bool mort)
 }
 
 // ---------------------------------------------------------------- tables
-__global__ void k2_tab_VP(float2* VP, int kind, int n, int sV) {
+__global__ void k2_tab_VP(float2* VP, Ph2 kind, int n, int sV) {
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= (int64_t(1) << (2 * sV)) * N) return;
@@ -104,7 +122,7 @@ __global__ void k2_tab_VP(float2* VP, int kind, int n, int sV) {
 }
 
 // groups g = tau 4^(L-s-1) + sigma', entries [g][o][c][t]
-__global__ void k2_tab_F(float2* F, int kind, Cheb5 ch, int n, int L, int s) {
+__global__ void k2_tab_F(float2* F, Ph2 kind, Cheb5 ch, int n, int L, int s) {
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N / 4 * 16 * R) return;
@@ -120,7 +138,7 @@ __global__ void k2_tab_F(float2* F, int kind, Cheb5 ch, int n, int L, int s) {
                 phi2(kind, sctr(s, tau, 0), sctr(s, tau, 1), g1, g2));
 }
 
-__global__ void k2_tab_M(float2* M, int kind, Cheb5 ch, int n, int L, int h) {
+__global__ void k2_tab_M(float2* M, Ph2 kind, int amp_kind, Cheb5 ch, int n, int L, int h) {
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N * R * R) return;
@@ -132,10 +150,11 @@ __global__ void k2_tab_M(float2* M, int kind, Cheb5 ch, int n, int L, int h) {
     const double y1 = sctr(h, tau, 0), y2 = sctr(h, tau, 1);
     const double g1 = fnode(ch, n, L - h, sg, 0, j / R1), g2 = fnode(ch, n, L - h, sg, 1, j % R1);
     const double e1 = fctr(n, L - h, sg, 0), e2 = fctr(n, L - h, sg, 1);
-    M[e] = expi(phi2(kind, z1, z2, g1, g2) - phi2(kind, z1, z2, e1, e2) - phi2(kind, y1, y2, g1, g2));
+    const float2 m = expi(phi2(kind, z1, z2, g1, g2) - phi2(kind, z1, z2, e1, e2) - phi2(kind, y1, y2, g1, g2));
+    M[e] = amp_kind == FIO_AMP_HANKEL ? cmul(hankel_amp(phi2_nl(kind.kind, kind.s, z1, z2, g1, g2)), m) : m;
 }
 
-__global__ void k2_tab_E(float2* E, int kind, Cheb5 ch, int n, int L, int s) {
+__global__ void k2_tab_E(float2* E, Ph2 kind, Cheb5 ch, int n, int L, int s) {
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N / 4 * 16 * R) return;
@@ -151,7 +170,7 @@ __global__ void k2_tab_E(float2* E, int kind, Cheb5 ch, int n, int L, int s) {
                 phi2(kind, z1, z2, fctr(n, L - s - 1, sq, 0), fctr(n, L - s - 1, sq, 1)));
 }
 
-__global__ void k2_tab_UP(float2* UP, int kind, int n, int L, int sU) {
+__global__ void k2_tab_UP(float2* UP, Ph2 kind, int n, int L, int sU) {
     const int64_t N = int64_t(n) * n;
     const int64_t nsg = int64_t(1) << (2 * (L - sU));
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -465,7 +484,9 @@ size_t off_QU(int NA) { return off_QV() + size_t(R) * NA; }
 
 }  // namespace
 
-bool bf2d_ok_kind(int kind) { return kind == FIO_PHASE_DFT || kind == FIO_PHASE_2D_ELLIPTIC; }
+bool bf2d_ok_kind(int kind) {
+    return kind == FIO_PHASE_DFT || kind == FIO_PHASE_2D_ELLIPTIC || kind == FIO_PHASE_2D_ISO;
+}
 
 fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
     const int n = bf->nside, L = bf->L, r1 = R1;
@@ -494,14 +515,14 @@ fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
     FIO_TRY(bf->P.ensure(P.size() * sizeof(float)));
     FIO_CUDA(cudaMemcpyAsync(bf->P.p, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     const int64_t N = int64_t(n) * n;
-    const int kind = bf->phase.kind;
+    const Ph2 kind{bf->phase.kind, bf->phase.s};
     const int64_t nVP = int64_t(NA) * N, nUP = N * NP, nM = N * R * R, nT = N / 4 * 16 * R;
     FIO_TRY(bf->VP.ensure(nVP * 8));
     FIO_TRY(bf->UP.ensure(nUP * 8));
     FIO_TRY(bf->M.ensure(nM * 8));
     k2_tab_VP<<<cdiv(nVP, TB), TB, 0, st>>>(bf->VP.as<float2>(), kind, n, bf->sV);
     k2_tab_UP<<<cdiv(nUP, TB), TB, 0, st>>>(bf->UP.as<float2>(), kind, n, L, bf->sU);
-    k2_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), kind, ch, n, L, bf->h);
+    k2_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), kind, bf->amp.kind, ch, n, L, bf->h);
     bf->C.resize(bf->h - bf->sV);
     for (int s = bf->sV; s < bf->h; ++s) {
         FIO_TRY(bf->C[s - bf->sV].ensure(nT * 8));

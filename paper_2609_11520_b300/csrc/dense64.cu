@@ -523,8 +523,9 @@ void big_scratch_free(BigScratch* b) {
     delete b;
 }
 
+int g_large_max_nodes = 16;
 void set_large_node_min(int m) { g_large_min = m; }
-bool large_level(int nodes, int m) { return nodes <= 16 && m >= g_large_min; }
+bool large_level(int nodes, int m) { return nodes <= g_large_max_nodes && m >= g_large_min; }
 
 // Node pass of a large level: per node t, Omega^+ and W = Y Omega^+, the null basis
 // Gamma, A = Y Gamma (in C) and the pivoted Cholesky of A^* A (FP64, at most `rhat`
@@ -860,6 +861,12 @@ fio_status big_ulv_root(BigScratch& b, int m0, const double2* Dp, float2* Rinv, 
 }
 
 }  // namespace fio
+
+extern "C" fio_status fio_set_large_node_count(int max_nodes) {
+    if (max_nodes < 1) return fio::fail(FIO_EINVAL, "fio_set_large_node_count: max_nodes must be >= 1");
+    fio::g_large_max_nodes = max_nodes;
+    return FIO_OK;
+}
 
 extern "C" fio_status fio_set_large_node(int m_min) {
     if (m_min < 1) return fio::fail(FIO_EINVAL, "fio_set_large_node: m_min must be >= 1");

@@ -27,12 +27,23 @@ def test_reference_arm_json_line():
 
 def test_roofline_entries():
     import bench
-    fused = bench.roofline_entry("k_bf_left_adj", 2.5, 8e8, 3e10, 6484.3, "measured", {"sm_max_mhz": 2032.0})
-    assert fused["bound"] == "alu" and fused["unit"] == "TFLOP/s"
+    fused = bench.roofline_entry("k_bf_left_adj", 2.5, 8e8, 3e10, 6484.3, "measured", {"sm_max_mhz": 2032.0}, 148)
+    assert fused["bound"] == "hbm" and fused["unit"] == "GB/s"
+    assert abs(fused["achieved"] - 8e8 / 2.5e-3 / 1e9) < 1e-9
     assert abs(fused["frac"] - fused["achieved"] / fused["peak"]) < 1e-12
-    assert abs(fused["peak"] - 148 * 128 * 2 * 2032e6 / 1e12) < 1e-9
-    hbm = bench.roofline_entry("k_ulv_up", 1.0, 6.4843e9, None, 6484.3, "measured", {})
+    eq = fused["fp32_equivalent"]
+    assert abs(eq["peak_tflops"] - 148 * 128 * 2 * 2032e6 / 1e12) < 1e-9
+    assert abs(eq["tflops"] - 2 * 3e10 / 2.5e-3 / 1e12) < 1e-9
+    hbm = bench.roofline_entry("k_ulv_up", 1.0, 6.4843e9, None, 6484.3, "measured", {}, 148)
     assert hbm["bound"] == "hbm" and hbm["unit"] == "GB/s" and abs(hbm["frac"] - 1.0) < 1e-6
+    assert "fp32_equivalent" not in hbm
     # bytes model: a per-level transfer launch moves the state twice plus its table
     b = bench.kernel_bytes("k_quad_ms", 1 << 16, 16, 64, {"L": 16, "sU": 13, "sV": 3, "h": 8}, {})
     assert b == 2 * (1 << 16) * 16 * 64 * 8 + 2 * (1 << 16) * 16 * 8
+
+
+def test_operator_ranks_from_the_stored_oracle_run():
+    import bench
+    ranks = bench.operator_ranks(1 << 16, 128)
+    assert ranks is not None and len(ranks) == 10 and ranks[0] == 0
+    assert bench.operator_ranks(1 << 14, 128) is None
