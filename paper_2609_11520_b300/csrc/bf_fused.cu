@@ -645,12 +645,20 @@ constexpr uint32_t kBBytesSM = 32 * 64 * 2, kBBytesMS = 32 * 32 * 2;   // one of
 
 struct Tc {
     uint32_t tmem;     // TMEM base address
-    uint64_t* mbar;    // MMA completion
+    uint64_t* mbar;    // MMA completion: one barrier per thread group (or one for the CTA)
     int* fail;         // shared flag: a bounded wait ran out
-    uint32_t phase;    // parity of the next completion of mbar
+    uint32_t phase;    // parity of the next completion of this thread's MMA barrier
     uint32_t bsm;      // shared address of B_hi; B_lo follows at + bbytes
     uint32_t bbytes;
+    bool grp;          // two independent thread groups (one per half of the columns)
 };
+
+// The CTA's threads split into two groups of NT / 2 that own disjoint columns (KC >= 2):
+// each group synchronizes on its own named barrier and issues its own MMAs.
+__device__ __forceinline__ int tgroup() { return threadIdx.x >> 8; }
+__device__ __forceinline__ void group_sync() {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + tgroup()), "r"(NT / 2) : "memory");
+}
 
 template <bool BF> struct Half16;
 template <> struct Half16<false> {
@@ -774,13 +782,16 @@ __device__ void level3_tc(float2* S, const float4* ph, int s, const Geo& g, Tc& 
         tc::tmem_wait_st();
     }
     tc::fence_before();
-    __syncthreads();
-    if (id == 0 && !*tc.fail) {
+    if (tc.grp) group_sync();
+    else __syncthreads();
+    const int issuer = tc.grp ? tgroup() * (NT / 2) : 0;
+    if (id == issuer && !*tc.fail) {
         tc::fence_after();
         const uint32_t idesc = tc::idesc_f16(BF, 128, 32);
         constexpr uint32_t sbo = MS ? 512 : 1024;
+        const int t_lo = tc.grp ? 2 * tgroup() : 0, t_hi = tc.grp ? t_lo + 2 : 4;
 #pragma unroll 1
-        for (int t4 = 0; t4 < 4; ++t4) {
+        for (int t4 = t_lo; t4 < t_hi; ++t4) {
             const uint32_t A = tc.tmem + 128 * t4, D = A + 64;
             if (MS) {
 #pragma unroll
@@ -858,12 +869,20 @@ __device__ void level3_tc(float2* S, const float4* ph, int s, const Geo& g, Tc& 
     tc::fence_before();
 }
 
-// CTA set-up of the tensor-core levels: TMEM (warp 0), mbarrier, B operands.
+// CTA set-up of the tensor-core levels: TMEM (warp 0), mbarriers, B operands.
+// s_mbar: [0, 1] MMA completion of group 0 / 1 (or [0] for the CTA), [2, 3] staging buffers
+// full, [4, 5] staging buffers consumed by both groups (grouped pipeline only).
 template <bool MS, bool BF>
-__device__ void tc_setup(Tc& tc, unsigned char* bsmem, const float* sPc, uint32_t* s_tmem, uint64_t* s_mbar, int* s_fail) {
+__device__ void tc_setup(Tc& tc, unsigned char* bsmem, const float* sPc, uint32_t* s_tmem, uint64_t* s_mbar, int* s_fail,
+                         bool grp) {
     if (threadIdx.x < 32) tc::tmem_alloc(s_tmem, kTmemCols);
     if (threadIdx.x == 0) {
-        tc::mbar_init(s_mbar, 1);
+        tc::mbar_init(s_mbar + 0, 1);
+        tc::mbar_init(s_mbar + 1, 1);
+        tc::mbar_init(s_mbar + 2, NT);
+        tc::mbar_init(s_mbar + 3, NT);
+        tc::mbar_init(s_mbar + 4, 2);
+        tc::mbar_init(s_mbar + 5, 2);
         *s_fail = 0;
     }
     build_b<MS, BF>(bsmem, sPc);
@@ -872,7 +891,8 @@ __device__ void tc_setup(Tc& tc, unsigned char* bsmem, const float* sPc, uint32_
     __syncthreads();
     tc::fence_after();
     tc.tmem = *s_tmem;
-    tc.mbar = s_mbar;
+    tc.grp = grp;
+    tc.mbar = s_mbar + (grp ? tgroup() : 0);
     tc.fail = s_fail;
     tc.phase = 0;
     tc.bsm = tc::smem_addr(bsmem);
@@ -973,6 +993,46 @@ __device__ void pipeline3(int nitem, int P, float4* buf0, float4* buf1, StageF s
     }
 }
 
+// The staged item sequence with two independent thread groups (tensor-core levels, KC >= 2, two
+// table buffers).  Every thread stages its share of each item with cp.async and arrives on the
+// buffer's `full` barrier once its copies complete; a group waits there, computes the item with
+// its own barriers, and one thread per group arrives on the buffer's `empty` barrier; the next
+// item for that buffer is staged only after both groups consumed it.  The groups drift apart by
+// up to one item, so one group's MMA waits overlap the other group's CUDA-core work.
+__device__ __forceinline__ void cp_arrive(uint64_t* m) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ void bounded_wait(uint64_t* m, uint32_t parity, int* fail) {
+    if (!*fail && !tc::mbar_wait(m, parity)) {
+        *fail = 1;
+        atomicExch(&g_tc_wait_timeout, 1);
+    }
+}
+template <class StageF, class ComputeF>
+__device__ void pipeline_grp(int nitem, float4* buf0, float4* buf1, StageF stage, ComputeF compute, uint64_t* bars,
+                             int* fail) {
+    uint64_t* full = bars + 2;
+    uint64_t* empty = bars + 4;
+    if (nitem == 0) return;
+    cp_arrive(&full[0]);   // item 0 was staged at the start of the kernel
+    for (int it = 0; it < nitem; ++it) {
+        const int b = it & 1;
+        if (it + 1 < nitem) {
+            const int b1 = (it + 1) & 1, use1 = (it + 1) >> 1;
+            if (use1 >= 1) bounded_wait(&empty[b1], uint32_t(use1 - 1) & 1u, fail);
+            stage(it + 1, b1 ? buf1 : buf0);
+            cp_arrive(&full[b1]);
+        }
+        bounded_wait(&full[b], uint32_t(it >> 1) & 1u, fail);
+        compute(it, b ? buf1 : buf0);
+        group_sync();
+        if ((threadIdx.x & (NT / 2 - 1)) == 0) mbar_arrive(&empty[b]);
+    }
+}
+
 template <bool ADJ, int MODE>
 __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
@@ -992,9 +1052,10 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     const int nitem = nlev + (ADJ ? 8 : 0);
     constexpr bool TC = MODE != kSimt;
     __shared__ uint32_t s_tmem;
-    __shared__ uint64_t s_mbar;
+    __shared__ uint64_t s_mbar[6];
     __shared__ int s_fail;
     Tc tc;
+    const bool grp = TC && nlev > 0 && KC >= 2 && nbuf3(P) == 2;
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
@@ -1024,7 +1085,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsU * R; e += NT) sPU[(e / R) * RS + e % R] = a.P[a.pu_off + e];
     __syncthreads();
-    if (TC && nlev > 0) tc_setup<!ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, &s_mbar, &s_fail);
+    if (TC && nlev > 0) tc_setup<!ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, s_mbar, &s_fail, grp);
     const int nB = nlev, lo = g.L - g.sU;
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U^*
@@ -1060,7 +1121,13 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             S[col * P * R + sw(slot, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i];
         }
     }
-    pipeline3(nitem, P, buf0, buf1, stage, compute);
+    if (grp) {
+        __syncthreads();
+        pipeline_grp(nitem, buf0, buf1, stage, compute, s_mbar, &s_fail);
+        __syncthreads();
+    } else {
+        pipeline3(nitem, P, buf0, buf1, stage, compute);
+    }
     if (ADJ) {
         for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
             const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
@@ -1120,9 +1187,10 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     const int nitem = nlev + (ADJ ? 0 : 8);
     constexpr bool TC = MODE != kSimt;
     __shared__ uint32_t s_tmem;
-    __shared__ uint64_t s_mbar;
+    __shared__ uint64_t s_mbar[6];
     __shared__ int s_fail;
     Tc tc;
+    const bool grp = TC && nlev > 0 && KC >= 2 && nbuf3(P) == 2;
     auto stage = [&](int it, float4* b) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
@@ -1152,7 +1220,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     for (int e = threadIdx.x; e < 2 * R * R; e += NT) sPc[(e / (R * R)) * PCS + e % (R * R)] = a.P[a.pc_off + e];
     for (int e = threadIdx.x; e < lsV * R; e += NT) sPV[(e / R) * RS + e % R] = a.P[e];
     __syncthreads();
-    if (TC && nlev > 0) tc_setup<ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, &s_mbar, &s_fail);
+    if (TC && nlev > 0) tc_setup<ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, s_mbar, &s_fail, grp);
     if (ADJ) {
         for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
             const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
@@ -1186,7 +1254,13 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             store_pair(S + col * P * R, aa * nl + rev_bits(leaf, g.h - g.sV), y);
         }
     }
-    pipeline3(nitem, P, buf0, buf1, stage, compute);
+    if (grp) {
+        __syncthreads();
+        pipeline_grp(nitem, buf0, buf1, stage, compute, s_mbar, &s_fail);
+        __syncthreads();
+    } else {
+        pipeline3(nitem, P, buf0, buf1, stage, compute);
+    }
     if (ADJ) {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // V^*
             const int col = id >> g.lgP, xl = id & (P - 1);
