@@ -57,7 +57,7 @@ def build(force=False, verbose=False):
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
-        ["-lcublas", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+        ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -5,7 +5,7 @@
 //
 // The one-CTA-per-node kernels apply Householder reflectors one at a time,
 // which streams O(m^2 r) data through one SM.  Here every step is a sequence
-// of batched GEMMs (cuBLAS, strided batched) and small blocked factorizations
+// of batched GEMMs (the library's own, gemm.cu) and small blocked factorizations
 // (one CTA per node and diagonal block):
 //   Omega^+ = Omega^* (Omega Omega^*)^{-1}, W = Y Omega^+   (Gram matrix, Cholesky)
 //   Gamma = orthonormal basis of null(Omega): (I - Omega^+ Omega) E for a
@@ -28,13 +28,12 @@
 // the root (whose sample block is nearly square), the Cholesky factorization
 // of the eliminated diagonal blocks of the ULV, the merge and the root
 // Cholesky.
-#include <cublas_v2.h>
-
 #include <mutex>
 #include <string>
 #include <type_traits>
 
 #include "cplx.cuh"
+#include "gemm.cuh"
 #include "hss.cuh"
 
 namespace fio {
@@ -55,52 +54,13 @@ template <class C> inline C cval(double re) {
     return v;
 }
 
-// ---------------------------------------------------------------- cuBLAS
-fio_status blas(cublasHandle_t* out, cudaStream_t st) {
-    static std::mutex mu;
-    static cublasHandle_t hs[64] = {};
-    int dev = 0;
-    FIO_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(FIO_EINVAL, "cuBLAS: device index out of range");
-    std::lock_guard<std::mutex> lock(mu);
-    if (!hs[dev] && cublasCreate(&hs[dev]) != CUBLAS_STATUS_SUCCESS) return fail(FIO_ECUDA, "cublasCreate failed");
-    if (cublasSetStream(hs[dev], st) != CUBLAS_STATUS_SUCCESS) return fail(FIO_ECUDA, "cublasSetStream failed");
-    *out = hs[dev];
-    return FIO_OK;
-}
-
-inline cublasStatus_t gemm_call(cublasHandle_t h, cublasOperation_t oa, cublasOperation_t ob, int m, int n, int k,
-                                const double2* al, const double2* A, int lda, long long sA, const double2* B, int ldb,
-                                long long sB, const double2* be, double2* C, int ldc, long long sC, int batch) {
-    return cublasZgemmStridedBatched(h, oa, ob, m, n, k, reinterpret_cast<const cuDoubleComplex*>(al),
-                                     reinterpret_cast<const cuDoubleComplex*>(A), lda, sA,
-                                     reinterpret_cast<const cuDoubleComplex*>(B), ldb, sB,
-                                     reinterpret_cast<const cuDoubleComplex*>(be), reinterpret_cast<cuDoubleComplex*>(C),
-                                     ldc, sC, batch);
-}
-inline cublasStatus_t gemm_call(cublasHandle_t h, cublasOperation_t oa, cublasOperation_t ob, int m, int n, int k,
-                                const float2* al, const float2* A, int lda, long long sA, const float2* B, int ldb,
-                                long long sB, const float2* be, float2* C, int ldc, long long sC, int batch) {
-    return cublasCgemmStridedBatched(h, oa, ob, m, n, k, reinterpret_cast<const cuComplex*>(al),
-                                     reinterpret_cast<const cuComplex*>(A), lda, sA, reinterpret_cast<const cuComplex*>(B),
-                                     ldb, sB, reinterpret_cast<const cuComplex*>(be), reinterpret_cast<cuComplex*>(C), ldc,
-                                     sC, batch);
-}
-
+// ---------------------------------------------------------------- GEMM
 // C = alpha op(A) op(B) + beta C for `batch` nodes (element strides sA, sB, sC); op: 'N' or 'C'.
+// The library's own batched complex GEMM (gemm.cu).
 template <class T>
 fio_status gemm(char ta, char tb, int m, int n, int k, double alpha, const T* A, int64_t lda, int64_t sA, const T* B,
                 int64_t ldb, int64_t sB, double beta, T* C, int64_t ldc, int64_t sC, int batch, cudaStream_t st) {
-    if (m <= 0 || n <= 0 || batch <= 0) return FIO_OK;
-    cublasHandle_t h;
-    FIO_TRY(blas(&h, st));
-    const T al = cval<T>(alpha), be = cval<T>(beta);
-    const cublasOperation_t oa = ta == 'C' ? CUBLAS_OP_C : CUBLAS_OP_N, ob = tb == 'C' ? CUBLAS_OP_C : CUBLAS_OP_N;
-    const cublasStatus_t s = gemm_call(h, oa, ob, m, n, std::max(k, 0), &al, A, int(lda), sA, B, int(ldb), sB, &be, C,
-                                       int(ldc), sC, batch);
-    if (s != CUBLAS_STATUS_SUCCESS)
-        return fail(FIO_ECUDA, "cublas gemm (strided batched) failed (" + std::to_string(int(s)) + ")");
-    return FIO_OK;
+    return bgemm<T>(ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
 }
 
 // ---------------------------------------------------------------- kernels
@@ -812,34 +772,43 @@ fio_status big_ulv_nodes(BigScratch& b, int nn, int m, int r, const double2* D, 
 
 // Merge (Eq. 2.12), FP64 (r x r products): parents t = 0..np-1, children 2t, 2t+1 of rank r;
 // D+ (2r x 2r) = [[D1, U1 B^* U2^*], [U2 B U1^*, D2]], U+ = [U1 Up_top; U2 Up_bot].
-fio_status big_ulv_merge(BigScratch& b, int np, int r, const double2* Dh22, const double2* Uh2, const float2* B,
-                         const float2* Up, int rp, double2* Dplus, double2* Uplus, cudaStream_t st) {
+// Merge into the parents (Eq. 2.12), every level and precision: D+ = [D^_22(1), (U2 B U1^*)^*; U2 B U1^*,
+// D^_22(2)] and U+ = [U^_1 0; 0 U^_2] U_p, the off-diagonal block and U+ as batched GEMMs over the
+// np parents (T = B U1^*, then U2 T).
+template <class C>
+fio_status ulv_merge_gemm(BigScratch& b, int np, int r, const C* Dh22, const C* Uh2, const float2* B, const float2* Up,
+                          int rp, C* Dplus, C* Uplus, cudaStream_t st) {
     const int m = 2 * r;
     const int64_t rr = int64_t(r) * r, mm = int64_t(m) * m;
-    FIO_TRY(b.Bz.ensure(size_t(np) * rr * 16));
-    FIO_TRY(b.Pz.ensure(size_t(np) * rr * 16));
-    z* Bz = b.Bz.as<z>();
-    z* T = b.Pz.as<z>();
-    k_cvt<c, z><<<g2(rr, np), TBD, 0, st>>>(B, r, rr, Bz, r, rr, r, r);
-    const z* U1 = Uh2;
-    const z* U2 = Uh2 + rr;
+    const size_t es = sizeof(C);
+    FIO_TRY(b.Bz.ensure(std::max<size_t>(16, size_t(np) * rr * es)));
+    FIO_TRY(b.Pz.ensure(std::max<size_t>(16, size_t(np) * rr * es)));
+    C* Bz = b.Bz.as<C>();
+    C* T = b.Pz.as<C>();
+    k_cvt<c, C><<<g2(rr, np), TBD, 0, st>>>(B, r, rr, Bz, r, rr, r, r);
+    const C* U1 = Uh2;
+    const C* U2 = Uh2 + rr;
     // T = B U1^*; lower-left = U2 T
-    FIO_TRY(gemm<z>('N', 'C', r, r, r, 1.0, Bz, r, rr, U1, r, 2 * rr, 0.0, T, r, rr, np, st));
-    FIO_TRY(gemm<z>('N', 'N', r, r, r, 1.0, U2, r, 2 * rr, T, r, rr, 0.0, Dplus + r, m, mm, np, st));
-    k_conjT<z><<<g2(rr, np), TBD, 0, st>>>(Dplus + r, m, mm, Dplus + int64_t(r) * m, m, mm, r, r);
-    k_cvt<z, z><<<g2(rr, np), TBD, 0, st>>>(Dh22, r, 2 * rr, Dplus, m, mm, r, r);
-    k_cvt<z, z><<<g2(rr, np), TBD, 0, st>>>(Dh22 + rr, r, 2 * rr, Dplus + r + int64_t(r) * m, m, mm, r, r);
+    FIO_TRY(gemm<C>('N', 'C', r, r, r, 1.0, Bz, r, rr, U1, r, 2 * rr, 0.0, T, r, rr, np, st));
+    FIO_TRY(gemm<C>('N', 'N', r, r, r, 1.0, U2, r, 2 * rr, T, r, rr, 0.0, Dplus + r, m, mm, np, st));
+    k_conjT<C><<<g2(rr, np), TBD, 0, st>>>(Dplus + r, m, mm, Dplus + int64_t(r) * m, m, mm, r, r);
+    k_cvt<C, C><<<g2(rr, np), TBD, 0, st>>>(Dh22, r, 2 * rr, Dplus, m, mm, r, r);
+    k_cvt<C, C><<<g2(rr, np), TBD, 0, st>>>(Dh22 + rr, r, 2 * rr, Dplus + r + int64_t(r) * m, m, mm, r, r);
     if (Up && rp > 0) {
         const int64_t mr = int64_t(m) * rp;
-        FIO_TRY(b.Upz.ensure(size_t(np) * mr * 16));
-        z* Upz = b.Upz.as<z>();
-        k_cvt<c, z><<<g2(mr, np), TBD, 0, st>>>(Up, m, mr, Upz, m, mr, m, rp);
-        FIO_TRY(gemm<z>('N', 'N', r, rp, r, 1.0, U1, r, 2 * rr, Upz, m, mr, 0.0, Uplus, m, mr, np, st));
-        FIO_TRY(gemm<z>('N', 'N', r, rp, r, 1.0, U2, r, 2 * rr, Upz + r, m, mr, 0.0, Uplus + r, m, mr, np, st));
+        FIO_TRY(b.Upz.ensure(size_t(np) * mr * es));
+        C* Upz = b.Upz.as<C>();
+        k_cvt<c, C><<<g2(mr, np), TBD, 0, st>>>(Up, m, mr, Upz, m, mr, m, rp);
+        FIO_TRY(gemm<C>('N', 'N', r, rp, r, 1.0, U1, r, 2 * rr, Upz, m, mr, 0.0, Uplus, m, mr, np, st));
+        FIO_TRY(gemm<C>('N', 'N', r, rp, r, 1.0, U2, r, 2 * rr, Upz + r, m, mr, 0.0, Uplus + r, m, mr, np, st));
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
 }
+template fio_status ulv_merge_gemm<float2>(BigScratch&, int, int, const float2*, const float2*, const float2*,
+                                           const float2*, int, float2*, float2*, cudaStream_t);
+template fio_status ulv_merge_gemm<double2>(BigScratch&, int, int, const double2*, const double2*, const float2*,
+                                            const float2*, int, double2*, double2*, cudaStream_t);
 
 // Root: D+ = L L^* (FP64), Rinv = L^{-*} L^{-1} (triangular inverse and product in FP32).
 fio_status big_ulv_root(BigScratch& b, int m0, const double2* Dp, float2* Rinv, int* d_status, cudaStream_t st) {

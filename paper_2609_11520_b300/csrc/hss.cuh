@@ -43,8 +43,9 @@ fio_status big_post(BigScratch& w, int nn, int rc, int mc, double2* Dcur, const 
                     float2* Bout, double2* Dnext, cudaStream_t st);
 fio_status big_ulv_nodes(BigScratch& b, int nn, int m, int r, const double2* D, const double2* U, float2* Wout,
                          double2* Dh22, double2* Uh2, int* d_status, cudaStream_t st);
-fio_status big_ulv_merge(BigScratch& b, int np, int r, const double2* Dh22, const double2* Uh2, const float2* B,
-                         const float2* Up, int rp, double2* Dplus, double2* Uplus, cudaStream_t st);
+template <class C>
+fio_status ulv_merge_gemm(BigScratch& b, int np, int r, const C* Dh22, const C* Uh2, const float2* B, const float2* Up,
+                          int rp, C* Dplus, C* Uplus, cudaStream_t st);
 fio_status big_ulv_root(BigScratch& b, int m0, const double2* Dp, float2* Rinv, int* d_status, cudaStream_t st);
 
 // Block products over the nodes of level l (column-major vectors, ld = rows):

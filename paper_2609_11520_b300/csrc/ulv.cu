@@ -205,59 +205,6 @@ __global__ void k_ulv_node(const float2* __restrict__ Df, const C* __restrict__ 
     }
 }
 
-// Merge into the parent (Eq. 2.12).  Children have rank r; parent transfer
-// U_p is (2r x rp), float2.  Outputs D+ (2r x 2r) and U+ (2r x rp) in C.
-template <class C>
-__global__ void k_ulv_merge(const C* __restrict__ Dh22, const C* __restrict__ Uh2, const float2* __restrict__ B, int r,
-                            const float2* __restrict__ Up, int rp, C* __restrict__ Dplus, C* __restrict__ Uplus) {
-    const int t = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-    const int m = 2 * r;
-    const C* D1 = Dh22 + int64_t(2 * t) * r * r;
-    const C* D2 = D1 + int64_t(r) * r;
-    const C* U1 = Uh2 + int64_t(2 * t) * r * r;
-    const C* U2 = U1 + int64_t(r) * r;
-    const float2* Bt = B + int64_t(t) * r * r;
-    C* Dp = Dplus + int64_t(t) * m * m;
-    // lower-left block: U2 B U1^*
-    for (int e = tid; e < m * m; e += bd) {
-        int i = e % m, j = e / m;
-        C a = czero<C>();
-        if (i < r && j < r) a = D1[i + j * r];
-        else if (i >= r && j >= r) a = D2[(i - r) + (j - r) * r];
-        else if (i >= r && j < r) {
-            // (U2 B U1^*)[i-r][j] = sum_p sum_q U2[i-r][p] B[p][q] conj(U1[j][q])
-            int ii = i - r;
-            for (int pp = 0; pp < r; ++pp) {
-                C bu = czero<C>();
-                for (int q = 0; q < r; ++q) gfma(bu, cvt<C>(Bt[pp + q * r]), gconj(U1[j + q * r]));
-                gfma(a, U2[ii + pp * r], bu);
-            }
-        } else {
-            // (U1 B^* U2^*)[i][j-r] = conj((U2 B U1^*)[j-r][i])
-            int jj = j - r;
-            C s = czero<C>();
-            for (int pp = 0; pp < r; ++pp) {
-                C bu = czero<C>();
-                for (int q = 0; q < r; ++q) gfma(bu, cvt<C>(Bt[pp + q * r]), gconj(U1[i + q * r]));
-                gfma(s, U2[jj + pp * r], bu);
-            }
-            a = gconj(s);
-        }
-        Dp[e] = a;
-    }
-    if (Up) {
-        const float2* Ut = Up + int64_t(t) * m * rp;
-        C* Upl = Uplus + int64_t(t) * m * rp;
-        for (int e = tid; e < m * rp; e += bd) {
-            int i = e % m, j = e / m;
-            const C* Ub = i < r ? U1 : U2;
-            int ii = i < r ? i : i - r, off = i < r ? 0 : r;
-            C a = czero<C>();
-            for (int q = 0; q < r; ++q) gfma(a, Ub[ii + q * r], cvt<C>(Ut[(off + q) + int64_t(j) * m]));
-            Upl[e] = a;
-        }
-    }
-}
 
 // Root: D+ = L L^*; Rinv = L^{-*} L^{-1} (complex64 column-major).
 __global__ void k_ulv_root(const double2* __restrict__ Dp, int m, float2* __restrict__ Rinv, double2* __restrict__ scr,
@@ -533,22 +480,17 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
             release();
             return s;
         }
-        if (mp > 0 && f64 && large_level(np, mp)) {
-            s = big_ulv_merge(*big, np, r, dh22[cur].as<double2>(), uh2[cur].as<double2>(), h->B[l - 1].as<float2>(), Up,
-                              rp, tmpD.as<double2>(), tmpU.as<double2>(), st);
+        if (mp > 0) {
+            s = f64 ? ulv_merge_gemm<double2>(*big, np, r, dh22[cur].as<double2>(), uh2[cur].as<double2>(),
+                                              h->B[l - 1].as<float2>(), Up, rp, tmpD.as<double2>(), tmpU.as<double2>(), st)
+                    : ulv_merge_gemm<float2>(*big, np, r, dh22[cur].as<float2>(), uh2[cur].as<float2>(),
+                                             h->B[l - 1].as<float2>(), Up, rp, tmpD.as<float2>(), tmpU.as<float2>(), st);
             if (s != FIO_OK) {
                 tmpD.release();
                 tmpU.release();
                 release();
                 return s;
             }
-        } else if (mp > 0) {
-            if (f64)
-                k_ulv_merge<double2><<<np, TB, 0, st>>>(dh22[cur].as<double2>(), uh2[cur].as<double2>(), h->B[l - 1].as<float2>(),
-                                                        r, Up, rp, tmpD.as<double2>(), tmpU.as<double2>());
-            else
-                k_ulv_merge<float2><<<np, TB, 0, st>>>(dh22[cur].as<float2>(), uh2[cur].as<float2>(), h->B[l - 1].as<float2>(),
-                                                       r, Up, rp, tmpD.as<float2>(), tmpU.as<float2>());
         }
         cudaError_t e = cudaStreamSynchronize(st);   // the scratch buffers are reused next level
         dplus.release();
