@@ -300,7 +300,12 @@ void hss_free(fio_hss* hss);
  * fio_batch_set_mode -- 0: one fio_solve per operator; 1: grouped launches
  *   (each stage one launch over all operators: the two fused BF half passes,
  *   one ULV node-product launch per tree depth, one for the roots); 2: the
- *   grouped launches captured once into a CUDA graph and replayed (default).
+ *   grouped launches captured once into a CUDA graph and replayed (default);
+ *   3: one persistent launch (one CTA per SM) that walks a device work list
+ *   of (stage, operator, block) items -- BF left and right half passes, ULV
+ *   up levels, roots, down levels -- each item waiting (bounded; a wait that
+ *   runs out is reported by fio_device_status) until the previous stage of
+ *   its own operator is complete, so operators advance independently.
  * fio_batch_solve -- F[i] = G~_i^{-1} K~_i^* U[i] for every i: U, F host
  *   arrays of n_ops device pointers to N_i x k[i] complex64 blocks with
  *   leading dimension N_i (U[i] and F[i] must not overlap).  The launch plan
@@ -309,7 +314,9 @@ void hss_free(fio_hss* hss);
  *   building it synchronizes the stream.
  * fio_batch_autotune -- times each candidate configuration (per-operator
  *   calls with the fused staged, fused unstaged or one-kernel-per-factor BF;
- *   grouped launches; grouped launches in a graph) over `reps` solves on
+ *   grouped launches; grouped launches in a graph; the persistent launch; the
+ *   grouped and persistent launches with the BF transfer levels on the CUDA
+ *   cores instead of the tensor cores) over `reps` solves on
  *   the given buffers, keeps the fastest, and writes one line per candidate
  *   ("name ms") into report (len bytes, may be NULL).
  * ---------------------------------------------------------------------- */
@@ -326,6 +333,13 @@ void fio_batch_free(fio_batch* batch);
  *   marks that launch's results invalid; the flag is cleared.  Synchronizes
  *   with the device (reads a device flag).  No paper counterpart. */
 fio_status fio_device_status(void);
+
+/* fio_selftest_wait_timeout -- runs the persistent batched kernel on a one-item
+ *   work list whose prerequisite never completes, so that the item's bounded
+ *   wait runs out (failure detection without a GPU fault; no paper
+ *   counterpart).  Returns FIO_ETIMEOUT (read back through fio_device_status,
+ *   which clears the flag) when the bound works; synchronizes `stream`. */
+fio_status fio_selftest_wait_timeout(void* stream);
 
 /* fio_last_error -- message of the last failing call on this thread. */
 const char* fio_last_error(void);

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fio_batch_free": (None, [P]),
     "fio_last_error": (ctypes.c_char_p, []),
     "fio_device_status": (I32, []),
+    "fio_selftest_wait_timeout": (I32, [P]),
     "fio_pcg": (I32, [P, P, P, P, I64, I32, ctypes.c_double, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double),
                       P]),
     "fio_profile_enable": (I32, [I32]),

@@ -226,7 +226,7 @@ class Batch:
     complex64 CUDA tensor per operator and returns the solutions.
     """
 
-    MODES = {"per_operator": 0, "grouped": 1, "graph": 2}
+    MODES = {"per_operator": 0, "grouped": 1, "graph": 2, "persistent": 3}
 
     def __init__(self, ops):
         self.ops = list(ops)

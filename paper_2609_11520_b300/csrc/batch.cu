@@ -14,6 +14,7 @@
 // fio_batch_autotune times the candidate configurations on the caller's
 // buffers (per-operator kernel path for mode 0: fused staged, fused
 // unstaged, one kernel per factor; modes 1 and 2) and keeps the fastest.
+#include <algorithm>
 #include <cstring>
 
 #include "bf.cuh"
@@ -38,6 +39,10 @@ struct fio_batch {
     fio::DevBuf ddesc, ditems, droots;
     std::vector<int> up_off, up_cnt, dn_off, dn_cnt;   // item ranges per launch
     int nroots = 0;
+    // persistent mode: work list and its counters
+    fio::DevBuf ditems_p, dctr_p;
+    int nitems_p = 0, nctr_p = 0;
+    int spin_limit = 1 << 20;   // polls of a dependency wait (~0.1 s at the poll interval)
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t capture_stream = nullptr;   // private: the caller's stream may be the legacy default stream
@@ -148,10 +153,95 @@ fio_status plan(fio_batch* b, const void* const* U, void* const* F, const int* k
         }
         b->dn_cnt[l] = int(items.size()) - b->dn_off[l];
     }
+    // ---- persistent work list: stages in dependency order, each item waiting on the counter of
+    // the previous stage of its own operator
+    {
+        std::vector<PItem> pl;
+        int nctr = 0;
+        std::vector<int> last_ctr(n, -1), last_target(n, 0);
+        std::vector<int> bidx;   // batch index of each grouped BF operator
+        for (int i = 0; i < n; ++i)
+            if (k[i] > 0 && std::find(b->fallback.begin(), b->fallback.end(), i) == b->fallback.end()) bidx.push_back(i);
+        const int nops = int(bidx.size());
+        std::vector<int> cl(nops, -1), nl(nops, 0), cr(nops, -1), nr(nops, 0);
+        for (const int4& v : li) {
+            if (cl[v.x] < 0) cl[v.x] = nctr++;
+            pl.push_back(PItem{kPLeft, v.x, v.y, v.z, 0, -1, 0, 0, -1, 0, cl[v.x], 0});
+            ++nl[v.x];
+        }
+        for (const int4& v : ri) {
+            if (cr[v.x] < 0) cr[v.x] = nctr++;
+            pl.push_back(PItem{kPRight, v.x, v.y, v.z, 0, -1, 0, 0, cl[v.x], nl[v.x], cr[v.x], 0});
+            ++nr[v.x];
+        }
+        for (int o = 0; o < nops; ++o) {
+            last_ctr[bidx[o]] = cr[o];
+            last_target[bidx[o]] = nr[o];
+        }
+        // node-product blocks of a stage go two to an item (one per half of the CTA)
+        auto add_stage = [&](int i, int type, const std::vector<int4>& its) {
+            if (its.empty()) return;
+            const int c = nctr++;
+            int cnt = 0;
+            const bool pair = type == kPUp || type == kPDown;
+            for (size_t j = 0; j < its.size(); j += pair ? 2 : 1) {
+                const int4 v = its[j];
+                PItem it{type, v.x, v.y, v.z, v.w, -1, 0, 0, last_ctr[i], last_target[i], c, 0};
+                if (pair && j + 1 < its.size()) {
+                    it.b2 = its[j + 1].y;
+                    it.c2 = its[j + 1].z;
+                    it.d2 = its[j + 1].w;
+                }
+                pl.push_back(it);
+                ++cnt;
+            }
+            last_ctr[i] = c;
+            last_target[i] = cnt;
+        };
+        std::vector<UlvGemmDesc> pdesc;
+        std::vector<UlvRootDesc> proots;
+        for (int d = 0; d < maxLh; ++d)
+            for (int i = 0; i < n; ++i) {
+                if (k[i] == 0 || plans[i].Lh <= d) continue;
+                const UlvGemmDesc& g = plans[i].up[plans[i].Lh - d];
+                if (g.nodes == 0) continue;
+                pdesc.push_back(g);
+                std::vector<int4> its;
+                ulv_gemm_items(g, int(pdesc.size()) - 1, its);
+                add_stage(i, kPUp, its);
+            }
+        for (int i = 0; i < n; ++i)
+            if (k[i] > 0 && plans[i].root.m > 0) {
+                proots.push_back(plans[i].root);
+                add_stage(i, kPRoot, {make_int4(int(proots.size()) - 1, 0, 0, 0)});
+            }
+        for (int l = 1; l <= maxLh; ++l)
+            for (int i = 0; i < n; ++i) {
+                if (k[i] == 0 || plans[i].Lh < l) continue;
+                const UlvGemmDesc& g = plans[i].down[l];
+                if (g.nodes == 0) continue;
+                pdesc.push_back(g);
+                std::vector<int4> its;
+                ulv_gemm_items(g, int(pdesc.size()) - 1, its);
+                add_stage(i, kPDown, its);
+            }
+        // the persistent list's own descriptor arrays follow the grouped ones in device memory
+        const int d0 = int(descs.size()), r0 = int(roots.size());
+        for (PItem& it : pl) {
+            if (it.type == kPUp || it.type == kPDown) it.a += d0;
+            if (it.type == kPRoot) it.a += r0;
+        }
+        b->nroots = r0;
+        descs.insert(descs.end(), pdesc.begin(), pdesc.end());
+        roots.insert(roots.end(), proots.begin(), proots.end());
+        FIO_TRY(upload(b->ditems_p, pl));
+        FIO_TRY(b->dctr_p.ensure(size_t(1 + nctr) * sizeof(int)));
+        b->nitems_p = int(pl.size());
+        b->nctr_p = nctr;
+    }
     FIO_TRY(upload(b->ddesc, descs));
     FIO_TRY(upload(b->ditems, items));
     FIO_TRY(upload(b->droots, roots));
-    b->nroots = int(roots.size());
     b->planned = true;
     return FIO_OK;
 }
@@ -169,6 +259,16 @@ fio_status launch_grouped(fio_batch* b, cudaStream_t st) {
     for (size_t l = 1; l < b->dn_off.size(); ++l)
         FIO_TRY(ulv_group_launch(dd, it + b->dn_off[l], b->dn_cnt[l], true, st));
     return FIO_OK;
+}
+
+// One persistent launch over the whole work list (after the K~^* of any operator the grouped
+// BF kernels do not cover).
+fio_status launch_persistent(fio_batch* b, cudaStream_t st) {
+    for (int i : b->fallback)
+        FIO_TRY(bf_apply(b->bfs[i], b->keyU[i], b->T.as<float2>() + b->Toff[i], b->bfs[i]->n, b->keyK[i], 1, st));
+    return batch_persistent_launch(b->dargs_l.p, b->dargs_r.p, b->ddesc.as<UlvGemmDesc>(), b->droots.as<UlvRootDesc>(),
+                                   b->ditems_p.as<PItem>(), b->nitems_p, b->dctr_p.as<int>(), b->nctr_p, b->bfmode,
+                                   b->spin_limit, st);
 }
 
 bool same_key(const fio_batch* b, const void* const* U, void* const* F, const int* k) {
@@ -200,7 +300,7 @@ extern "C" fio_status fio_batch_create(fio_bf* const* bfs, fio_hss* const* hss, 
 }
 
 extern "C" fio_status fio_batch_set_mode(fio_batch* b, int mode) {
-    if (!b || mode < 0 || mode > 2) return fail(FIO_EINVAL, "fio_batch_set_mode: bad mode");
+    if (!b || mode < 0 || mode > 3) return fail(FIO_EINVAL, "fio_batch_set_mode: bad mode");
     b->mode = mode;
     return FIO_OK;
 }
@@ -223,6 +323,7 @@ extern "C" fio_status fio_batch_solve(fio_batch* b, const void* const* U, void* 
     }
     if (!b->planned || !same_key(b, U, F, k)) FIO_TRY(plan(b, U, F, k));
     if (b->mode == 1) return launch_grouped(b, st);
+    if (b->mode == 3) return launch_persistent(b, st);
     if (!b->gexec) {
         FIO_TRY(launch_grouped(b, st));   // first run eagerly (also sets kernel attributes)
         FIO_CUDA(cudaStreamSynchronize(st));
@@ -253,13 +354,28 @@ extern "C" fio_status fio_batch_autotune(fio_batch* b, const void* const* U, voi
                                          void* stream, char* report, int64_t len) {
     if (!b || reps < 1) return fail(FIO_EINVAL, "fio_batch_autotune: bad arguments");
     cudaStream_t st = as_stream(stream);
+    // knobs: launch structure (per operator / grouped / graph / one persistent launch), BF kernels
+    // of the per-operator mode, and the transfer-level arithmetic (tensor cores or CUDA cores)
     struct Cand {
-        int mode, path;
+        int mode, path, simt;
         const char* name;
     };
-    const Cand cands[] = {{0, 2, "per-operator, fused staged"}, {0, 3, "per-operator, fused unstaged"},
-                          {0, 1, "per-operator, one kernel per factor"}, {1, 0, "grouped launches"},
-                          {2, 0, "grouped launches in a CUDA graph"}};
+    const Cand cands[] = {{0, 2, 0, "per-operator, fused staged"},
+                          {0, 3, 0, "per-operator, fused unstaged"},
+                          {0, 1, 0, "per-operator, one kernel per factor"},
+                          {1, 0, 0, "grouped launches"},
+                          {2, 0, 0, "grouped launches in a CUDA graph"},
+                          {3, 0, 0, "one persistent launch over a work list"},
+                          {1, 0, 1, "grouped launches, CUDA-core transfer levels"},
+                          {3, 0, 1, "one persistent launch, CUDA-core transfer levels"}};
+    std::vector<bool> simt0;
+    for (auto* bf : b->bfs) simt0.push_back(bf->simt);
+    auto set_simt = [&](int v) {
+        for (auto* bf : b->bfs)
+            if (bf_v3_ok(bf)) bf->simt = v != 0;
+        b->planned = false;
+        drop_graph(b);
+    };
     cudaEvent_t e0, e1;
     FIO_CUDA(cudaEventCreate(&e0));
     FIO_CUDA(cudaEventCreate(&e1));
@@ -269,6 +385,7 @@ extern "C" fio_status fio_batch_autotune(fio_batch* b, const void* const* U, voi
     for (int c = 0; c < int(sizeof(cands) / sizeof(cands[0])); ++c) {
         b->mode = cands[c].mode;
         b->path0 = cands[c].path;
+        set_simt(cands[c].simt);
         bool ok = true;
         if (cands[c].mode == 0)
             for (auto* bf : b->bfs)
@@ -304,7 +421,13 @@ extern "C" fio_status fio_batch_autotune(fio_batch* b, const void* const* U, voi
     if (bi < 0) return fail(FIO_EINVAL, "fio_batch_autotune: no candidate applies");
     b->mode = cands[bi].mode;
     b->path0 = cands[bi].path;
-    for (auto* bf : b->bfs) bf_set_path(bf, 0);
+    for (size_t i = 0; i < b->bfs.size(); ++i) {
+        bf_set_path(b->bfs[i], 0);
+        b->bfs[i]->simt = simt0[i];
+    }
+    if (cands[bi].simt) set_simt(1);
+    b->planned = false;
+    drop_graph(b);
     rep += std::string("chosen: ") + cands[bi].name + "\n";
     if (report && len > 0) {
         std::strncpy(report, rep.c_str(), size_t(len) - 1);
@@ -321,4 +444,31 @@ extern "C" void fio_batch_free(fio_batch* b) {
                       &b->droots})
         d->release();
     delete b;
+}
+
+extern "C" fio_status fio_selftest_wait_timeout(void* stream) {
+    // A one-item work list whose prerequisite counter nothing increments: the item's bounded wait
+    // must run out (about 1000 polls), set the device flag and let the kernel finish.
+    cudaStream_t st = as_stream(stream);
+    fio::DevBuf d_items, d_root, d_ctr;
+    auto release = [&]() {
+        d_items.release();
+        d_root.release();
+        d_ctr.release();
+    };
+    const PItem it{kPRoot, 0, 0, 0, 0, -1, 0, 0, 0, 1, 1, 0};
+    const UlvRootDesc rd{nullptr, nullptr, nullptr, 0, 0};
+    fio_status s = upload(d_items, std::vector<PItem>{it});
+    if (s == FIO_OK) s = upload(d_root, std::vector<UlvRootDesc>{rd});
+    if (s == FIO_OK) s = d_ctr.ensure(3 * sizeof(int));
+    if (s == FIO_OK)
+        s = batch_persistent_launch(nullptr, nullptr, nullptr, d_root.as<UlvRootDesc>(), d_items.as<PItem>(), 1,
+                                    d_ctr.as<int>(), 2, 1, 1000, st);
+    if (s == FIO_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "fio_selftest_wait_timeout");
+    }
+    release();
+    if (s != FIO_OK) return s;
+    return fio_device_status();
 }

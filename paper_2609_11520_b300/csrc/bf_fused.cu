@@ -28,7 +28,9 @@
 #include <cstring>
 
 #include "bf.cuh"
+#include "hss.cuh"
 #include "tc.cuh"
+#include "ulv_body.cuh"
 
 namespace fio {
 namespace {
@@ -1382,9 +1384,132 @@ fio_status right3(const fio_bf* bf, const HalfArgs& a, int kcols, cudaStream_t s
     return FIO_OK;
 }
 
+// ---------------------------------------------------------------- persistent batched solve
+// One launch for the whole batched online stage (f = G~^{-1} K~^* u of many operators): a
+// grid of one CTA per SM walks a device work list of (stage, operator, block) items in
+// dependency order -- BF left half passes, right half passes, ULV up levels, roots, ULV down
+// levels.  A CTA takes the next item with an atomic, waits (thread 0, bounded spin) until the
+// item's prerequisite counter reaches its target -- the number of items of the previous stage
+// of the same operator -- runs it, and counts it done.  Items wait only on items taken before
+// them by running CTAs, so the walk cannot deadlock; a wait that runs out sets a device flag
+// (reported as FIO_ETIMEOUT by fio_device_status) and the item proceeds.
+__device__ int g_persist_timeout = 0;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1) k_batch_persistent(const HalfArgs* __restrict__ largs,
+                                                            const HalfArgs* __restrict__ rargs,
+                                                            const UlvGemmDesc* __restrict__ udesc,
+                                                            const UlvRootDesc* __restrict__ rdesc,
+                                                            const PItem* __restrict__ items, int nitems,
+                                                            int* __restrict__ head, int* __restrict__ counters,
+                                                            int spin_limit) {
+    extern __shared__ float4 smem4[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(head, 1);
+            s_item = i;
+            if (i < nitems && items[i].dep >= 0) {
+                const PItem it = items[i];
+                int n = 0;
+                while (ld_acquire(counters + it.dep) < it.target) {
+                    if (++n > spin_limit) {
+                        atomicExch(&g_persist_timeout, 1);
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        const int i = s_item;
+        if (i >= nitems) break;
+        const PItem it = items[i];
+        if (it.type == kPLeft) {
+            left3_body<true, MODE>(largs[it.a], it.b, it.c);
+        } else if (it.type == kPRight) {
+            right3_body<true, MODE>(rargs[it.a], it.b, it.c);
+        } else if (it.type == kPRoot) {
+            if (threadIdx.x < ulvb::kUlvThreads) {
+                const UlvRootDesc& g = rdesc[it.a];
+                ulvb::root_body(g.A, g.m, g.x, g.y, g.k, threadIdx.x);
+            }
+        } else {
+            // two node-product blocks of one stage, one per half of the CTA (own tiles and barrier)
+            const int half = threadIdx.x / ulvb::kUlvThreads, tid = threadIdx.x % ulvb::kUlvThreads;
+            const int t = half ? it.b2 : it.b, c0 = half ? it.c2 : it.c, r0 = half ? it.d2 : it.d;
+            if (t >= 0) {
+                float2* sx = reinterpret_cast<float2*>(smem4) + half * ulvb::WT * (ulvb::KCOL + ulvb::RB);
+                float2* sw = sx + ulvb::WT * ulvb::KCOL;
+                auto sync = [half] {
+                    if (half) asm volatile("bar.sync 4, 256;" ::: "memory");
+                    else asm volatile("bar.sync 3, 256;" ::: "memory");
+                };
+                const UlvGemmDesc& g = udesc[it.a];
+                if (it.type == kPUp)
+                    ulvb::node_gemm_body<false>(g.W, g.m, g.inA, g.nA, g.ldA, g.inB, g.ldB, g.outC, g.nC, g.ldC, g.outD,
+                                                g.ldD, g.k, t, c0, r0, sx, sw, sync, tid);
+                else
+                    ulvb::node_gemm_body<true>(g.W, g.m, g.inA, g.nA, g.ldA, g.inB, g.ldB, g.outC, g.nC, g.ldC, g.outD,
+                                               g.ldD, g.k, t, c0, r0, sx, sw, sync, tid);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(counters + it.done, 1);
+        }
+    }
+}
+
 }  // namespace v3
 
 }  // namespace
+
+fio_status batch_persistent_launch(const void* dleft_args, const void* dright_args, const UlvGemmDesc* udesc,
+                                   const UlvRootDesc* rdesc, const PItem* items, int nitems, int* head_and_counters,
+                                   int ncounters, int mode, int spin_limit, cudaStream_t st) {
+    if (nitems == 0) return FIO_OK;
+    FIO_TRY(v3::set_attrs3());
+    static PerDeviceOnce attrs;
+    FIO_CUDA(attrs.run([] {
+        const void* fns[] = {(const void*)v3::k_batch_persistent<v3::kSimt>, (const void*)v3::k_batch_persistent<v3::kTcF16>,
+                             (const void*)v3::k_batch_persistent<v3::kTcBF16>};
+        for (const void* f : fns) {
+            const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(v3::kSmem3Max));
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }));
+    int dev = 0, sms = 0;
+    FIO_CUDA(cudaGetDevice(&dev));
+    FIO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FIO_CUDA(cudaMemsetAsync(head_and_counters, 0, sizeof(int) * (1 + ncounters), st));
+    const int grid = std::min(sms, nitems);
+    const HalfArgs* la = static_cast<const HalfArgs*>(dleft_args);
+    const HalfArgs* ra = static_cast<const HalfArgs*>(dright_args);
+    int* head = head_and_counters;
+    int* ctr = head_and_counters + 1;
+    const size_t sm = v3::kSmem3Max;
+    if (mode == v3::kTcF16)
+        FIO_LAUNCH("k_batch_persistent", st, (v3::k_batch_persistent<v3::kTcF16><<<grid, v3::NT, sm, st>>>(
+                                                 la, ra, udesc, rdesc, items, nitems, head, ctr, spin_limit)));
+    else if (mode == v3::kTcBF16)
+        FIO_LAUNCH("k_batch_persistent", st, (v3::k_batch_persistent<v3::kTcBF16><<<grid, v3::NT, sm, st>>>(
+                                                 la, ra, udesc, rdesc, items, nitems, head, ctr, spin_limit)));
+    else
+        FIO_LAUNCH("k_batch_persistent", st, (v3::k_batch_persistent<v3::kSimt><<<grid, v3::NT, sm, st>>>(
+                                                 la, ra, udesc, rdesc, items, nitems, head, ctr, spin_limit)));
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
 
 // ---------------------------------------------------------------- grouped
 // Host tables of a grouped half-pass launch over several operators.
@@ -1493,13 +1618,13 @@ int bf_fused_mode(const fio_bf* bf, int prec) {
 }
 
 int tc_wait_timeouts() {
-    int v = 0;
+    int v = 0, w = 0;
     if (cudaMemcpyFromSymbol(&v, v3::g_tc_wait_timeout, sizeof(int)) != cudaSuccess) return -1;
-    if (v) {
-        const int z = 0;
-        cudaMemcpyToSymbol(v3::g_tc_wait_timeout, &z, sizeof(int));
-    }
-    return v;
+    if (cudaMemcpyFromSymbol(&w, v3::g_persist_timeout, sizeof(int)) != cudaSuccess) return -1;
+    const int z = 0;
+    if (v) cudaMemcpyToSymbol(v3::g_tc_wait_timeout, &z, sizeof(int));
+    if (w) cudaMemcpyToSymbol(v3::g_persist_timeout, &z, sizeof(int));
+    return v | w;
 }
 
 bool bf_v3_ok(const fio_bf* bf) {

@@ -67,6 +67,16 @@ struct UlvGemmDesc {
     int64_t ldA, ldB, ldC, ldD;
     int m, nA, nC, k, nodes;
 };
+// One item of the persistent batched solve: type (kP*), payload (a, b, c, d), for ULV node
+// products a second block (a, b2, c2, d2) of the same stage run by the other half of the CTA
+// (b2 < 0: none), the counter it waits on (dep, -1 for none) until it reaches `target`, and the
+// counter it increments.
+enum { kPLeft = 0, kPRight = 1, kPUp = 2, kPRoot = 3, kPDown = 4 };
+struct PItem {
+    int type, a, b, c, d;
+    int b2, c2, d2;
+    int dep, target, done, pad;
+};
 struct UlvRootDesc {
     const float2* A;   // m x m
     const float2* x;   // m x k (ld m)
@@ -83,4 +93,9 @@ fio_status ulv_solve_plan(fio_hss* h, const float2* B, float2* X, int64_t ld, in
 void ulv_gemm_items(const UlvGemmDesc& d, int di, std::vector<int4>& items);
 fio_status ulv_group_launch(const UlvGemmDesc* dd, const int4* ditems, int nitems, bool down, cudaStream_t st);
 fio_status ulv_root_group_launch(const UlvRootDesc* dd, int n, cudaStream_t st);
+// The persistent batched solve (bf_fused.cu): one launch over the work list `items`;
+// head_and_counters: 1 + ncounters ints (zeroed here), mode: transfer-level mode of the BF items.
+fio_status batch_persistent_launch(const void* dleft_args, const void* dright_args, const UlvGemmDesc* udesc,
+                                   const UlvRootDesc* rdesc, const PItem* items, int nitems, int* head_and_counters,
+                                   int ncounters, int mode, int spin_limit, cudaStream_t st);
 }

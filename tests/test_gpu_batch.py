@@ -36,7 +36,7 @@ def test_batch_modes_equal_per_operator(ops):
     Us = [to_dev(crandn(bf.n, k, seed=100 + i)) for i, ((bf, _), k) in enumerate(zip(ops, ks))]
     refs = [to_np(fio_solve(bf, h, U)) for (bf, h), U in zip(ops, Us)]
     b = Batch(ops)
-    for mode in ("per_operator", "grouped", "graph"):
+    for mode in ("per_operator", "grouped", "graph", "persistent"):
         b.set_mode(mode)
         Fs = [torch.empty_like(U) for U in Us]
         for rep in range(3):   # graph: eager + capture, then replays
@@ -85,7 +85,7 @@ def test_batched_workload_operators():
     assert all(0.5 <= s <= 1.0 for _, s in ops_)
 
 
-@pytest.mark.parametrize("mode", ["grouped", "graph"])
+@pytest.mark.parametrize("mode", ["grouped", "graph", "persistent"])
 def test_batch_matches_oracle(mode):
     """Grouped launches and their graph replay against the FP64 oracle (Algorithm 1 per operator):
     three operators of different N and s, each with its own oracle FIOSolver on the same Philox
@@ -120,3 +120,31 @@ def test_batch_matches_oracle(mode):
         assert e_g <= 2 * e_o + 1e-5, (bf.n, e_g, e_o)
         ref = to_np(h.solve(to_dev(S.bf.adjoint(u))))
         assert rel(to_np(F), ref) < 1e-4, bf.n
+
+
+def test_persistent_replans_and_sees_new_inputs(ops):
+    from paper_2609_11520_b300 import Batch, device_status, fio_solve
+    b = Batch(ops).set_mode("persistent")
+    Us = [to_dev(crandn(bf.n, 3, seed=700 + i)) for i, (bf, _) in enumerate(ops)]
+    Fs = b.solve(Us)
+    for i, U in enumerate(Us):
+        U.copy_(to_dev(crandn(ops[i][0].n, 3, seed=800 + i)))
+    b.solve(Us, Fs)
+    torch.cuda.synchronize()
+    for (bf, h), U, F in zip(ops, Us, Fs):
+        assert rel(to_np(F), to_np(fio_solve(bf, h, U))) < 1e-5
+    device_status()   # no dependency wait ran out
+
+
+def test_persistent_wait_runs_out_and_is_reported():
+    """Failure detection without a GPU fault: a work item whose prerequisite never completes must
+    end its bounded wait, let the kernel finish, and surface as FIO_ETIMEOUT; the flag clears."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    from paper_2609_11520_b300 import _lib, device_status
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert _lib.lib.fio_selftest_wait_timeout(st) == _lib.FIO_ETIMEOUT
+    device_status()   # cleared: raises nothing
+    x = torch.ones(4, device="cuda")
+    assert float((x + 1).sum()) == 8.0   # the context is still usable
