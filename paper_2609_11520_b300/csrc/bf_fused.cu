@@ -1035,6 +1035,36 @@ __device__ void pipeline_grp(int nitem, float4* buf0, float4* buf1, StageF stage
     }
 }
 
+// Middle state between HBM and the shared state, in 16-byte chunks (two coefficients), eight
+// chunks per thread in flight: goff(col, lp) is the float2 offset of pair lp's coefficients in
+// `mid` (column col of the CTA), slot(lp) its physical slot.
+template <bool IN, class GOff, class Slot>
+__device__ __forceinline__ void mid_copy(float2* S, float2* mid, int P, int KC, int kc, GOff goff, Slot slot) {
+    constexpr int kBatch = 8;
+    const int per_col = P * (R / 2), nch = per_col * KC;
+    for (int base = threadIdx.x; base < nch; base += NT * kBatch) {
+        float4 v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int id = base + u * NT, col = id / per_col, rem = id - col * per_col, lp = rem >> 3, i2 = rem & 7;
+            if (id < nch && col < kc) {
+                const int p = slot(lp);
+                if (IN) v[u] = reinterpret_cast<const float4*>(mid + goff(col, lp))[i2];
+                else v[u] = reinterpret_cast<const float4*>(S + col * P * R + p * R)[i2 ^ (p & 7)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int id = base + u * NT, col = id / per_col, rem = id - col * per_col, lp = rem >> 3, i2 = rem & 7;
+            if (id < nch && col < kc) {
+                const int p = slot(lp);
+                if (IN) reinterpret_cast<float4*>(S + col * P * R + p * R)[i2 ^ (p & 7)] = v[u];
+                else reinterpret_cast<float4*>(mid + goff(col, lp))[i2] = v[u];
+            }
+        }
+    }
+}
+
 template <bool ADJ, int MODE>
 __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     extern __shared__ float4 smem4[];
@@ -1116,12 +1146,9 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             store_pair(S + col * P * R, lp, y);
         }
     } else {
-        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
-            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
-            if (col >= kc) continue;
-            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB);
-            S[col * P * R + sw(slot, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i];
-        }
+        mid_copy<true>(S, a.mid, P, KC, kc,   // middle state in
+                       [&](int col, int lp) { return (int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R; },
+                       [&](int lp) { return (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB); });
     }
     if (grp) {
         __syncthreads();
@@ -1131,12 +1158,9 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
         pipeline3(nitem, P, buf0, buf1, stage, compute);
     }
     if (ADJ) {
-        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
-            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
-            if (col >= kc) continue;
-            const int slot = (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB);
-            a.mid[(int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R + i] = S[col * P * R + sw(slot, i)];
-        }
+        mid_copy<false>(S, a.mid, P, KC, kc,   // middle state out
+                        [&](int col, int lp) { return (int64_t(col0 + col) * a.n + int64_t(box) * P + lp) * R; },
+                        [&](int lp) { return (rev_bits(lp & ((1 << nB) - 1), nB) << lo) | (lp >> nB); });
     } else {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // U
             const int col = id >> g.lgP, xl = id & (P - 1);
@@ -1224,11 +1248,9 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     __syncthreads();
     if (TC && nlev > 0) tc_setup<ADJ, MODE == kTcBF16>(tc, bsm, sPc, &s_tmem, s_mbar, &s_fail, grp);
     if (ADJ) {
-        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state in
-            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
-            if (col >= kc) continue;
-            S[col * P * R + sw(lp, i)] = a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i];
-        }
+        mid_copy<true>(S, a.mid, P, KC, kc,   // middle state in
+                       [&](int col, int lp) { return (int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R; },
+                       [](int lp) { return lp; });
     } else {
         for (int id = threadIdx.x; id < P * KC; id += NT) {   // V
             const int col = id >> g.lgP, lp = id & (P - 1);
@@ -1293,11 +1315,9 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             a.Y[int64_t(col0 + col) * a.ldy + xg] = out;
         }
     } else {
-        for (int id = threadIdx.x; id < P * R * KC; id += NT) {   // middle state out
-            const int col = id / (P * R), rem = id - col * P * R, lp = rem / R, i = rem % R;
-            if (col >= kc) continue;
-            a.mid[(int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R + i] = S[col * P * R + sw(lp, i)];
-        }
+        mid_copy<false>(S, a.mid, P, KC, kc,   // middle state out
+                        [&](int col, int lp) { return (int64_t(col0 + col) * a.n + int64_t(lp) * nmid + box) * R; },
+                        [](int lp) { return lp; });
     }
     if (TC && nlev > 0) tc_teardown(tc);
 }
