@@ -507,6 +507,9 @@ extern "C" fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, i
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_status(e, "bf_build: table kernels"));
     bf->table_bytes = (nVP + nUP + nM + nT * int64_t(bf->C.size() + bf->B.size())) * 8 + int64_t(P.size()) * 4;
+    if ((s = bf_prestage(bf, st)) != FIO_OK) return cleanup(s);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_status(e, "bf_build: staged tables"));
     *out = bf;
     return FIO_OK;
 }
@@ -607,5 +610,9 @@ extern "C" void bf_free(fio_bf* bf) {
     bf->VP.release(); bf->UP.release(); bf->M.release(); bf->P.release(); bf->ws.release();
     for (auto& b : bf->C) b.release();
     for (auto& b : bf->B) b.release();
+    for (int d = 0; d < 2; ++d) {
+        for (auto& b : bf->Cst[d]) b.release();
+        for (auto& b : bf->Bst[d]) b.release();
+    }
     delete bf;
 }

@@ -43,6 +43,9 @@ struct fio_bf {
     fio::DevBuf VP, UP, M, P;      // P: PV | PU | Pc (float)
     std::vector<fio::DevBuf> C;    // index s - sV
     std::vector<fio::DevBuf> B;    // index s - h
+    // C and B tables pre-arranged in the staged shared-memory layout of the fused passes, per
+    // direction ([0] forward, [1] adjoint); empty where the staged fused kernels do not apply
+    std::vector<fio::DevBuf> Cst[2], Bst[2];
     fio::DevBuf ws;                // two coefficient states
     int64_t table_bytes = 0;
     bool force_unfused = false;    // use the per-level kernels even where the fused pass applies
@@ -63,6 +66,8 @@ int bf_fused_kc(const fio_bf* bf);
 // prec: -1 the handle's precision setting, 0 FP32, 1 split BF16.
 fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, float2* mid,
                           cudaStream_t st, int prec = -1);
+// Pre-arrange the C and B tables in the staged layout of the fused kernels (bf_v3_ok handles).
+fio_status bf_prestage(fio_bf* bf, cudaStream_t st);
 // Transfer-level mode of the staged fused kernels (0 CUDA cores, 1 tensor cores FP16 parts,
 // 2 tensor cores BF16 parts) for the given precision request.
 int bf_fused_mode(const fio_bf* bf, int prec);

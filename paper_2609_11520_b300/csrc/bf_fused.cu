@@ -249,6 +249,8 @@ struct HalfArgs {
     const float* P;      // PV | PU | Pc
     int pu_off, pc_off;
     Tabs tab;            // left: E tables by s - h ; right: F tables by s - sV
+    Tabs tabs;           // the same tables pre-arranged in the staged shared-memory layout of this
+                         // direction (box-major slices of P * 256 B), or null: copied by TMA
     int n, L, h, sU, sV, k;
     int mode;            // transfer levels of the staged kernels: kSimt, kTcF16 or kTcBF16
 };
@@ -489,6 +491,42 @@ __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0
 struct Geo {
     int L, h, sU, sV, n, P, lgP, KC;   // KC * P = NT
 };
+
+// Position in the staged buffer of 16-byte chunk e of a box's phase slice of level s: rows by
+// physical quad (row = qi*4 + o*2 + e, o the lane-varying output half, e the summed input half),
+// chunk m of a row at m ^ ((row >> 1) & 7).
+template <bool LEFT, bool ADJ>
+__device__ __forceinline__ int stage_pos(int e, int s, const Geo& g) {
+    const int W = LEFT ? g.L - s : g.h - s;
+    const int j = LEFT ? g.sU - s : g.h - s;
+    const int half = 1 << (W - 1);
+    const int m = e & 7, row = e >> 3;
+    const int ql = row >> 2, c = (row >> 1) & 1, be = row & 1;
+    const int a = ql >> (W - 1), lo = ql & (half - 1);
+    int rr;
+    if (LEFT) {
+        const int wj = W - j;
+        rr = (rev_bits(lo & ((1 << (j - 1)) - 1), j - 1) << wj) | (lo >> (j - 1));
+    } else {
+        rr = rev_bits(lo, W - 1);
+    }
+    const int qi = (a << (W - 1)) | rr;
+    const int o = ADJ ? be : c, ee = ADJ ? c : be;
+    const int drow = qi * 4 + o * 2 + ee;
+    return drow * 8 + (m ^ ((drow >> 1) & 7));
+}
+
+// The staged layout of every box of one level, in global memory (one CTA per box): the
+// tensor-core passes then stage a level with one TMA bulk copy.
+template <bool LEFT, bool ADJ>
+__global__ void k_prestage(float4* __restrict__ dst, const float2* __restrict__ T, Geo g, int s) {
+    const int box = blockIdx.x;
+    const int64_t q0 = LEFT ? (int64_t(box) << (g.L - g.h - 1)) : (int64_t(box) << (g.h - 1));
+    const float4* src = reinterpret_cast<const float4*>(T + q0 * 4 * R);
+    float4* d = dst + int64_t(box) * g.P * 16;
+    const int nch = (g.P / 2) * 4 * 8;
+    for (int e = threadIdx.x; e < nch; e += blockDim.x) d[stage_pos<LEFT, ADJ>(e, s, g)] = src[e];
+}
 
 // Stage the phase slice of level s (contiguous in global memory) into `buf`.
 template <bool LEFT, bool ADJ>
@@ -1013,20 +1051,36 @@ __device__ __forceinline__ void bounded_wait(uint64_t* m, uint32_t parity, int* 
         atomicExch(&g_tc_wait_timeout, 1);
     }
 }
+// TMA bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) into this CTA's
+// shared memory, completing on the mbarrier: thread 0 arms the barrier with the byte count and
+// issues the copy, every other thread arrives.
+__device__ __forceinline__ void bulk_stage(float4* dst, const float4* src, uint32_t bytes, uint64_t* full) {
+    if (threadIdx.x == 0) {
+        tc::mbar_expect_tx(full, bytes);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_addr(dst)),
+                     "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_addr(full))
+                     : "memory");
+    } else {
+        mbar_arrive(full);
+    }
+}
+
+// stage(it, buf, full) issues item it's copies into buf and arrives on `full` (one arrival per
+// thread, by cp_arrive after cp.async copies or through bulk_stage).
 template <class StageF, class ComputeF>
 __device__ void pipeline_grp(int nitem, float4* buf0, float4* buf1, StageF stage, ComputeF compute, uint64_t* bars,
                              int* fail) {
     uint64_t* full = bars + 2;
     uint64_t* empty = bars + 4;
     if (nitem == 0) return;
-    cp_arrive(&full[0]);   // item 0 was staged at the start of the kernel
+    stage(0, buf0, &full[0]);
     for (int it = 0; it < nitem; ++it) {
         const int b = it & 1;
         if (it + 1 < nitem) {
             const int b1 = (it + 1) & 1, use1 = (it + 1) >> 1;
             if (use1 >= 1) bounded_wait(&empty[b1], uint32_t(use1 - 1) & 1u, fail);
-            stage(it + 1, b1 ? buf1 : buf0);
-            cp_arrive(&full[b1]);
+            stage(it + 1, b1 ? buf1 : buf0, &full[b1]);
         }
         bounded_wait(&full[b], uint32_t(it >> 1) & 1u, fail);
         compute(it, b ? buf1 : buf0);
@@ -1096,6 +1150,24 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             stage_m<true>(b, a.M, box, it - nlev, g);
         }
     };
+    // grouped pipeline: pre-staged level slices and the contiguous M^* chunks by TMA bulk copies
+    auto stage_grp = [&](int it, float4* b, uint64_t* full) {
+        if (it < nlev) {
+            const int s = ADJ ? g.sU - 1 - it : g.h + it;
+            if (a.tabs.t[s - g.h]) {
+                bulk_stage(b, reinterpret_cast<const float4*>(a.tabs.t[s - g.h]) + int64_t(box) * P * 16,
+                           uint32_t(P) * 256, full);
+                return;
+            }
+            stage_level<true, ADJ>(b, a.tab.t[s - g.h], box, s, g);
+        } else {
+            const int CH = P / 8;
+            bulk_stage(b, reinterpret_cast<const float4*>(a.M + (int64_t(box) * P + (it - nlev) * CH) * R * R),
+                       uint32_t(CH) * R * R * 8, full);
+            return;
+        }
+        cp_arrive(full);
+    };
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.sU - 1 - it : g.h + it;
@@ -1110,7 +1182,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
             mchunk3<true>(S, cur, it - nlev, g);
         }
     };
-    if (nitem > 0) {
+    if (nitem > 0 && !grp) {
         stage(0, buf0);
         cp_commit();
     }
@@ -1152,7 +1224,7 @@ __device__ void left3_body(const HalfArgs& a, int box, int col0) {
     }
     if (grp) {
         __syncthreads();
-        pipeline_grp(nitem, buf0, buf1, stage, compute, s_mbar, &s_fail);
+        pipeline_grp(nitem, buf0, buf1, stage_grp, compute, s_mbar, &s_fail);
         __syncthreads();
     } else {
         pipeline3(nitem, P, buf0, buf1, stage, compute);
@@ -1225,6 +1297,22 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             stage_m<false>(b, a.M, box, it - nlev, g);
         }
     };
+    // grouped pipeline: pre-staged level slices by TMA bulk copies (the strided M chunks of the
+    // forward pass stay on cp.async)
+    auto stage_grp = [&](int it, float4* b, uint64_t* full) {
+        if (it < nlev) {
+            const int s = ADJ ? g.h - 1 - it : g.sV + it;
+            if (a.tabs.t[s - g.sV]) {
+                bulk_stage(b, reinterpret_cast<const float4*>(a.tabs.t[s - g.sV]) + int64_t(box) * P * 16,
+                           uint32_t(P) * 256, full);
+                return;
+            }
+            stage_level<false, ADJ>(b, a.tab.t[s - g.sV], box, s, g);
+        } else {
+            stage_m<false>(b, a.M, box, it - nlev, g);
+        }
+        cp_arrive(full);
+    };
     auto compute = [&](int it, const float4* cur) {
         if (it < nlev) {
             const int s = ADJ ? g.h - 1 - it : g.sV + it;
@@ -1239,7 +1327,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             mchunk3<false>(S, cur, it - nlev, g);
         }
     };
-    if (nitem > 0) {
+    if (nitem > 0 && !grp) {
         stage(0, buf0);
         cp_commit();
     }
@@ -1280,7 +1368,7 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
     }
     if (grp) {
         __syncthreads();
-        pipeline_grp(nitem, buf0, buf1, stage, compute, s_mbar, &s_fail);
+        pipeline_grp(nitem, buf0, buf1, stage_grp, compute, s_mbar, &s_fail);
         __syncthreads();
     } else {
         pipeline3(nitem, P, buf0, buf1, stage, compute);
@@ -1561,6 +1649,9 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
         HalfArgs al = a, ar = a;
         for (size_t i = 0; i < bf->B.size() && i < 24; ++i) al.tab.t[i] = bf->B[i].as<float2>();
         for (size_t i = 0; i < bf->C.size() && i < 24; ++i) ar.tab.t[i] = bf->C[i].as<float2>();
+        const int dir = adjoint ? 1 : 0;
+        for (size_t i = 0; i < bf->Bst[dir].size() && i < 24; ++i) al.tabs.t[i] = bf->Bst[dir][i].as<float2>();
+        for (size_t i = 0; i < bf->Cst[dir].size() && i < 24; ++i) ar.tabs.t[i] = bf->Cst[dir][i].as<float2>();
         // adjoint: left reads X, writes mid; right reads mid, writes Y.  forward: the reverse.
         if (adjoint) {
             al.X = ops[o].X;
@@ -1637,6 +1728,39 @@ int bf_fused_mode(const fio_bf* bf, int prec) {
     return bf->simt ? v3::kSimt : v3::kTcF16;
 }
 
+fio_status bf_prestage(fio_bf* bf, cudaStream_t st) {
+    using namespace v3;
+    if (!bf_v3_ok(bf)) return FIO_OK;
+    const int64_t bytes = int64_t(bf->n) / 2 * 4 * R * 8;   // one level's table
+    for (int side = 0; side < 2; ++side) {                   // 0 right (C levels), 1 left (B levels)
+        Geo g;
+        g.L = bf->L; g.h = bf->h; g.sU = bf->sU; g.sV = bf->sV; g.n = bf->n;
+        g.lgP = side ? bf->L - bf->h : bf->h;
+        g.P = 1 << g.lgP;
+        g.KC = NT >> g.lgP;
+        const int nbox = side ? 1 << bf->h : 1 << (bf->L - bf->h);
+        std::vector<DevBuf>* dst = side ? bf->Bst : bf->Cst;
+        const std::vector<DevBuf>& src = side ? bf->B : bf->C;
+        const int s0 = side ? bf->h : bf->sV;
+        for (int adj = 0; adj < 2; ++adj) {
+            dst[adj].resize(src.size());
+            for (size_t i = 0; i < src.size(); ++i) {
+                FIO_TRY(dst[adj][i].ensure(size_t(bytes)));
+                float4* d = dst[adj][i].as<float4>();
+                const float2* t = src[i].as<float2>();
+                const int s = s0 + int(i);
+                if (side && adj) k_prestage<true, true><<<nbox, 256, 0, st>>>(d, t, g, s);
+                else if (side) k_prestage<true, false><<<nbox, 256, 0, st>>>(d, t, g, s);
+                else if (adj) k_prestage<false, true><<<nbox, 256, 0, st>>>(d, t, g, s);
+                else k_prestage<false, false><<<nbox, 256, 0, st>>>(d, t, g, s);
+            }
+        }
+    }
+    FIO_CUDA(cudaGetLastError());
+    bf->table_bytes += 2 * int64_t(bf->C.size() + bf->B.size()) * bytes;
+    return FIO_OK;
+}
+
 int tc_wait_timeouts() {
     int v = 0, w = 0;
     if (cudaMemcpyFromSymbol(&v, v3::g_tc_wait_timeout, sizeof(int)) != cudaSuccess) return -1;
@@ -1693,6 +1817,10 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
         HalfArgs al = a, ar = a;
         al.tab = tl;
         ar.tab = tr;
+        al.tabs = Tabs{};
+        ar.tabs = Tabs{};
+        for (size_t i = 0; i < bf->Bst[adjoint ? 1 : 0].size() && i < 24; ++i) al.tabs.t[i] = bf->Bst[adjoint ? 1 : 0][i].as<float2>();
+        for (size_t i = 0; i < bf->Cst[adjoint ? 1 : 0].size() && i < 24; ++i) ar.tabs.t[i] = bf->Cst[adjoint ? 1 : 0][i].as<float2>();
         if (adjoint) {
             FIO_TRY(v3::left3<true>(bf, al, kcols, st));
             FIO_TRY(v3::right3<true>(bf, ar, kcols, st));
