@@ -610,6 +610,7 @@ extern "C" void bf_free(fio_bf* bf) {
     bf->VP.release(); bf->UP.release(); bf->M.release(); bf->P.release(); bf->ws.release();
     for (auto& b : bf->C) b.release();
     for (auto& b : bf->B) b.release();
+    bf->Mst.release();
     for (int d = 0; d < 2; ++d) {
         for (auto& b : bf->Cst[d]) b.release();
         for (auto& b : bf->Bst[d]) b.release();

@@ -46,6 +46,7 @@ struct fio_bf {
     // C and B tables pre-arranged in the staged shared-memory layout of the fused passes, per
     // direction ([0] forward, [1] adjoint); empty where the staged fused kernels do not apply
     std::vector<fio::DevBuf> Cst[2], Bst[2];
+    fio::DevBuf Mst;               // M in the staged layout of the forward right half
     fio::DevBuf ws;                // two coefficient states
     int64_t table_bytes = 0;
     bool force_unfused = false;    // use the per-level kernels even where the fused pass applies

@@ -251,6 +251,7 @@ struct HalfArgs {
     Tabs tab;            // left: E tables by s - h ; right: F tables by s - sV
     Tabs tabs;           // the same tables pre-arranged in the staged shared-memory layout of this
                          // direction (box-major slices of P * 256 B), or null: copied by TMA
+    const float2* Ms;    // right half, forward: M pre-arranged in the staged layout, or null
     int n, L, h, sU, sV, k;
     int mode;            // transfer levels of the staged kernels: kSimt, kTcF16 or kTcBF16
 };
@@ -569,6 +570,19 @@ __device__ void stage_m(float4* buf, const float2* __restrict__ M, int box, int 
         const float4* src = reinterpret_cast<const float4*>(M + pg * R * R) + i * 8 + m;
         const int pos = LEFT ? m : (m ^ (i & 7));
         cp16(buf + (pl * R + i) * 8 + pos, src);
+    }
+}
+
+// The forward middle-factor chunks of every right-half box in their staged layout (box-major,
+// 8 chunks of P/8 pairs each), for one TMA bulk copy per chunk.
+__global__ void k_prestage_m(float4* __restrict__ dst, const float2* __restrict__ M, Geo g) {
+    const int box = blockIdx.x, ck = blockIdx.y;
+    const int CH = g.P / 8, nch = CH * R * 8;
+    float4* d = dst + (int64_t(box) * 8 + ck) * nch;
+    for (int e = threadIdx.x; e < nch; e += blockDim.x) {
+        const int m = e & 7, i = (e >> 3) & (R - 1), pl = e >> 7;
+        const int64_t pg = int64_t(ck * CH + pl) * (int64_t(1) << (g.L - g.h)) + box;
+        d[(pl * R + i) * 8 + (m ^ (i & 7))] = reinterpret_cast<const float4*>(M + pg * R * R)[i * 8 + m];
     }
 }
 
@@ -1309,6 +1323,12 @@ __device__ void right3_body(const HalfArgs& a, int box, int col0) {
             }
             stage_level<false, ADJ>(b, a.tab.t[s - g.sV], box, s, g);
         } else {
+            if (a.Ms) {
+                const int nch = (P / 8) * R * 8;
+                bulk_stage(b, reinterpret_cast<const float4*>(a.Ms) + (int64_t(box) * 8 + (it - nlev)) * nch,
+                           uint32_t(nch) * 16, full);
+                return;
+            }
             stage_m<false>(b, a.M, box, it - nlev, g);
         }
         cp_arrive(full);
@@ -1652,6 +1672,8 @@ void bf_group_tables(const std::vector<BfGroupOp>& ops, int adjoint, std::vector
         const int dir = adjoint ? 1 : 0;
         for (size_t i = 0; i < bf->Bst[dir].size() && i < 24; ++i) al.tabs.t[i] = bf->Bst[dir][i].as<float2>();
         for (size_t i = 0; i < bf->Cst[dir].size() && i < 24; ++i) ar.tabs.t[i] = bf->Cst[dir][i].as<float2>();
+        al.Ms = nullptr;
+        ar.Ms = (!adjoint && bf->Mst.p) ? bf->Mst.as<float2>() : nullptr;
         // adjoint: left reads X, writes mid; right reads mid, writes Y.  forward: the reverse.
         if (adjoint) {
             al.X = ops[o].X;
@@ -1756,8 +1778,17 @@ fio_status bf_prestage(fio_bf* bf, cudaStream_t st) {
             }
         }
     }
+    {   // the forward middle factor for the right half
+        Geo g;
+        g.L = bf->L; g.h = bf->h; g.sU = bf->sU; g.sV = bf->sV; g.n = bf->n;
+        g.lgP = bf->h;
+        g.P = 1 << g.lgP;
+        g.KC = NT >> g.lgP;
+        FIO_TRY(bf->Mst.ensure(bf->M.bytes));
+        k_prestage_m<<<dim3(1 << (bf->L - bf->h), 8), 256, 0, st>>>(bf->Mst.as<float4>(), bf->M.as<float2>(), g);
+    }
     FIO_CUDA(cudaGetLastError());
-    bf->table_bytes += 2 * int64_t(bf->C.size() + bf->B.size()) * bytes;
+    bf->table_bytes += 2 * int64_t(bf->C.size() + bf->B.size()) * bytes + int64_t(bf->M.bytes);
     return FIO_OK;
 }
 
@@ -1790,7 +1821,7 @@ int bf_fused_kc(const fio_bf* bf) {
 
 fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kcols, int adjoint,
                           float2* mid, cudaStream_t st, int prec) {
-    HalfArgs a;
+    HalfArgs a{};
     a.X = X;
     a.ldx = ld;
     a.Y = Y;
@@ -1821,6 +1852,8 @@ fio_status bf_apply_fused(const fio_bf* bf, const float2* X, float2* Y, int64_t 
         ar.tabs = Tabs{};
         for (size_t i = 0; i < bf->Bst[adjoint ? 1 : 0].size() && i < 24; ++i) al.tabs.t[i] = bf->Bst[adjoint ? 1 : 0][i].as<float2>();
         for (size_t i = 0; i < bf->Cst[adjoint ? 1 : 0].size() && i < 24; ++i) ar.tabs.t[i] = bf->Cst[adjoint ? 1 : 0][i].as<float2>();
+        al.Ms = nullptr;
+        ar.Ms = (!adjoint && bf->Mst.p) ? bf->Mst.as<float2>() : nullptr;
         if (adjoint) {
             FIO_TRY(v3::left3<true>(bf, al, kcols, st));
             FIO_TRY(v3::right3<true>(bf, ar, kcols, st));
