@@ -37,6 +37,19 @@ def bump_centers(N, m=10, seed=7):
     return np.stack([rng.uniform(0.0, 1.0, m), rng.uniform(-N / 2, N / 2, m)], axis=1)
 
 
+def sample_entries(N, S, seed=8, ncols=None):
+    """S index pairs (rows, cols) uniform over [0, N) x [0, N) (int64), for the sampled-entry error
+    of the adaptive BF rank; with ncols the columns are drawn from ncols distinct values only."""
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, N, S, dtype=np.int64)
+    if ncols is None:
+        cols = rng.integers(0, N, S, dtype=np.int64)
+    else:
+        pool = rng.choice(N, size=ncols, replace=False).astype(np.int64)
+        cols = pool[rng.integers(0, ncols, S)]
+    return rows, cols
+
+
 def batched_operators(count=32, seed=4, logs=(12, 13, 14, 15, 16, 17)):
     """(N, s) per operator: N uniform over 2^logs, s ~ U[0.5, 1]."""
     rng = np.random.default_rng(seed)
