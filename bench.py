@@ -178,7 +178,12 @@ def parse_profile(text):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel build:
 # (kernel name, N, columns per launch, transfer-level arithmetic) -> bytes, or absent.
-NCU_TRAFFIC = {}
+# `python bench.py --profile-case bf_adjoint --n 65536 --k 64 --reps 1` under
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (one launch of each half pass).
+NCU_TRAFFIC = {
+    ("k_bf_left_adj", 65536, 64, "tc_f16"): 256577280 + 489624320,
+    ("k_bf_right_adj", 65536, 64, "tc_f16"): 625194752 + 31775744,
+}
 
 
 def roofline_entry(name, per_launch_ms, nbytes, nfma, hbm_peak, peak_src, clocks, sm_count, traffic=None):
@@ -271,26 +276,26 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def kernel2d_bytes(name, N, kc, sV, L, sU):
+def kernel2d_bytes(name, N, kc, sV, L, sU, R=25):
     """Algorithmic HBM bytes of one 2D kernel launch (kc columns): coefficient states
-    N*25*kc complex64 in and out, the vectors, and each table read once."""
-    S = N * 25 * kc * 8
+    N*R*kc complex64 in and out (R = r1^2), the vectors, and each table read once."""
+    S = N * R * kc * 8
     vec = N * kc * 8
     if name.startswith("k2_V"):
         return S + vec + (4 ** sV) * N * 8
     if name.startswith("k2_U"):
         return S + vec + N * (4 ** (L - sU)) * 8
     if name.startswith("k2_C") or name.startswith("k2_B"):
-        return 2 * S + N * 4 * 25 * 8
+        return 2 * S + N * 4 * R * 8
     if name.startswith("k2_M"):
-        return 2 * S + N * 625 * 8
+        return 2 * S + N * R * R * 8
     return None
 
 
 def run_2d(args):
-    """2D workload: the K~^* apply of the quadtree BF at n = 256 (N = 2^16, r = 25) on
-    blocks of k = 16 RHS, and the full online solve at a smaller n (default 64) with its
-    offline stages timed."""
+    """2D workload: the K~^* apply of the quadtree BF at n = 256 (N = 2^16, r = r1^2, r1 = --r1-2d,
+    default 5) on blocks of k = 16 RHS, and the full online solve at n = --n2d (default 64) with
+    its offline stages timed."""
     import torch
     from paper_2609_11520_b300 import BF, HSS, fio_solve
     from paper_2609_11520_b300 import _lib
@@ -298,7 +303,8 @@ def run_2d(args):
     stream = torch.cuda.current_stream()
     n, k = 256, 16
     N = n * n
-    bf = BF(n, 25, "elliptic2d")
+    R = args.r1_2d ** 2
+    bf = BF(n, R, "elliptic2d")
     info = bf.info()
     rng = np.random.default_rng(3)
     X = torch.from_numpy((rng.standard_normal((k, N)) + 1j * rng.standard_normal((k, N))).astype(np.complex64)).cuda()
@@ -337,17 +343,17 @@ def run_2d(args):
     peak, peak_src = load_peaks()
     kernels = {}
     for name, (cnt, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        nb = kernel2d_bytes(name, N, k, info["sV"], info["L"], info["sU"])
+        nb = kernel2d_bytes(name, N, k, info["sV"], info["L"], info["sU"], R)
         gbs = nb / (ms / cnt / 1e3) / 1e9 if nb else None
         kernels[name] = {"launches": cnt, "ms_total": round(ms, 4), "share": round(ms / tot, 4),
                          "bytes_per_launch": nb, "achieved_gbs": gbs}
     top = max(prof.items(), key=lambda kv: kv[1][1])
-    tb = kernel2d_bytes(top[0], N, k, info["sV"], info["L"], info["sU"])
+    tb = kernel2d_bytes(top[0], N, k, info["sV"], info["L"], info["sU"], R)
     ach = tb / (top[1][1] / top[1][0] / 1e3) / 1e9
     # full solve at a smaller n
     ns = args.n2d
     t0 = time.perf_counter()
-    bs = BF(ns, 25, "elliptic2d")
+    bs = BF(ns, R, "elliptic2d")
     g = HSS.from_samples(bf=bs, leaf=256, oversample=10, tol=1e-3, seed=1)
     t_hss = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -362,17 +368,17 @@ def run_2d(args):
     fio_solve(bs, g, U, out=OUT, refine_steps=1)
     e1 = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
     line = {
-        "metric": "2D K~^* apply RHS/s (n = 256, N = 2^16, quadtree BF r = 25); 2D online solve", "unit": UNIT,
+        "metric": f"2D K~^* apply RHS/s (n = 256, N = 2^16, quadtree BF r = {R}); 2D online solve", "unit": UNIT,
         "value": k * args.steps / (sum(adj) / 1e3), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(adj), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
-        "config": {"workload": "2d: Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), a = 1, n = 256, r = 25, k = 16 per apply",
+        "config": {"workload": f"2d: Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), a = 1, n = 256, r = {R}, k = 16 per apply",
                    "l2": "flushed between timed steps (256 MiB write)", "table_bytes": info["table_bytes"]},
         "forward": {"value": k * args.steps / (sum(fwd) / 1e3), "ms_per_step": statistics.mean(fwd)},
         "kernels": kernels,
         "roofline": {"kernel": top[0], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "peak_source": peak_src, "bytes_per_launch": tb, "traffic": None},
-        "solve": {"n": ns, "N": ns * ns, "leaf": 256, "tol": 1e-3, "k": k, "hss_build_s": round(t_hss, 2),
+        "solve": {"n": ns, "N": ns * ns, "r": R, "leaf": 256, "tol": 1e-3, "k": k, "hss_build_s": round(t_hss, 2),
                   "ulv_factor_s": round(t_fac, 2), "ranks": g.info()["ranks"], "rhs_per_s": k * args.steps / (sum(sol) / 1e3),
                   "ms_per_solve": statistics.mean(sol), "e_direct_vs_f_true": e, "e_refine1": e1},
         "clocks": clk.summary(),
@@ -425,7 +431,7 @@ def batched_leg(steps, warmup, count=32):
 SERVING_1D = [(1 << 14, 1.0), (1 << 15, 1.0), (1 << 16, 1.0), (1 << 16, 0.5), (1 << 17, 1.0), (1 << 18, 1.0)]
 
 
-def serving_leg(nreq, rates=(0.5, 0.8, 1.0), ops2d=(64,), seed=5):
+def serving_leg(nreq, rates=(0.5, 0.8, 1.0), ops2d=(128, 256), seed=5, r2d=49, prebuilt=None):
     """Config-5 workload through the continuous-batching server: resident operators (the six 1D
     operators of SERVING_1D and 2D elliptic operators with n per dimension in ops2d), Poisson
     arrivals (seed 5) at the given fractions of the measured saturated request rate, 1..32 RHS per
@@ -440,7 +446,10 @@ def serving_leg(nreq, rates=(0.5, 0.8, 1.0), ops2d=(64,), seed=5):
         bf = BF(n, 16, "cabs", sdepth)
         ops[f"1d_n{n}_s{sdepth}"] = (bf, HSS.from_samples(bf=bf, leaf=128, oversample=10, tol=1e-3, seed=70 + i).factor())
     for i, n2 in enumerate(ops2d):
-        bf = BF(n2, 25, "elliptic2d")
+        if prebuilt and (n2, r2d) in prebuilt:
+            ops[f"2d_n{n2}"] = prebuilt[(n2, r2d)]
+            continue
+        bf = BF(n2, r2d, "elliptic2d")
         ops[f"2d_n{n2}"] = (bf, HSS.from_samples(bf=bf, leaf=256, oversample=10, tol=1e-3, seed=90 + i).factor())
     t_build = time.perf_counter() - t0
     names = sorted(ops)
@@ -474,9 +483,64 @@ def serving_leg(nreq, rates=(0.5, 0.8, 1.0), ops2d=(64,), seed=5):
             "requests_per_rate": nreq, "saturated": {k_: round(v, 4) if isinstance(v, float) else v for k_, v in sat.items()},
             "by_rate_fraction": by_rate, "offline_build_s": round(t_build, 2), "operators": names,
             "workload": "continuous batching over resident operators (1D N = 2^14, 2^15, 2^16, 2^16 with s = 0.5, "
-                        "2^17, 2^18; 2D elliptic n = %s), Poisson arrivals (seed 5), 1..32 RHS per request, kmax 64, "
-                        "4 streams, pinned host requests (H2D and D2H inside the latency); p50/p99 at the highest "
-                        "rate fraction, rhs_per_s saturated" % ", ".join(str(x) for x in ops2d)}
+                        "2^17, 2^18; 2D elliptic n = %s, BF r = %d), Poisson arrivals (seed 5), 1..32 RHS per request, "
+                        "kmax 64, 4 streams, pinned host requests (H2D and D2H inside the latency); p50/p99 at the "
+                        "highest rate fraction, rhs_per_s saturated" % (", ".join(str(x) for x in ops2d), r2d)}
+
+
+def c3_leg(steps, warmup, n=256, r1=7, k=16):
+    """2D end-to-end solve (n = 256, N = 2^16, HSS leaf 256 = 16 x 16, tol 1e-3, 16 RHS): offline BF,
+    HSS construction and ULV timed once; the online f = F~ K~^* u timed on device-resident blocks
+    with L2 flushed.  u = K~ f_true.  The BF runs on the r1 x r1 grid (default 7 x 7 = 49): the
+    sampled FP64 entry errors of the 5 x 5 and 7 x 7 grids are reported beside it (at 5 x 5 the BF
+    error lies above the HSS tolerance and the HSS ranks grow past what fits the offline budget).
+    Returns (summary, (bf, hss))."""
+    import torch
+    from fio_inputs import sample_entries
+    from paper_2609_11520_b300 import BF, HSS, entry_error, fio_solve
+    N = n * n
+    rows, cols = sample_entries(N, 2000, seed=9)
+    e_grid = {f"{q}x{q}": entry_error(n, q * q, rows, cols, "elliptic2d") for q in (5, 6, 7)}
+    t0 = time.perf_counter()
+    bf = BF(n, r1 * r1, "elliptic2d")
+    torch.cuda.synchronize()
+    t_bf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = HSS.from_samples(bf=bf, leaf=256, oversample=10, tol=1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_hss = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.factor()
+    torch.cuda.synchronize()
+    t_fac = time.perf_counter() - t0
+    f = crandn(N, k, seed=0)
+    Ft = torch.from_numpy(np.ascontiguousarray(f.T.astype(np.complex64))).cuda()
+    U = bf.apply(Ft)
+    OUT = torch.empty_like(U)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        fio_solve(bf, g, U, out=OUT)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fio_solve(bf, g, U, out=OUT)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    e = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
+    fio_solve(bf, g, U, out=OUT, refine_steps=1)
+    e1 = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
+    ms = statistics.median(ts)
+    return ({"rhs_per_s": k / (ms / 1e3), "ms_per_solve": ms, "k": k, "n": n, "N": N, "r": r1 * r1,
+             "offline_s": {"bf_build": round(t_bf, 3), "hss_build": round(t_hss, 2), "ulv_factor": round(t_fac, 2)},
+             "hss_ranks": g.info()["ranks"], "e_direct_vs_f_true": e, "e_refine1": e1,
+             "bf_entry_error_by_grid": e_grid,
+             "workload": "2D Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), a = 1, n = 256, BF r1 x r1 = %d x %d, "
+                         "HSS leaf 256 (16 x 16), oversample 10, tol 1e-3, 16 RHS per solve, u = K~ f_true, "
+                         "L2 flushed between timed solves" % (r1, r1)}, (bf, g))
 
 
 def run_batched(args):
@@ -565,10 +629,11 @@ def main():
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--workload", default="large1d", choices=["large1d", "batched1d", "serving", "2d"])
     ap.add_argument("--n2d", type=int, default=64)
+    ap.add_argument("--r1-2d", type=int, default=5, help="2D tensor grid r1 (rank r1^2) of --workload 2d")
     ap.add_argument("--requests", type=int, default=10000)
-    ap.add_argument("--serve-2d", default="64", help="n per dimension of the 2D serving operators, comma separated")
+    ap.add_argument("--serve-2d", default="128,256", help="n per dimension of the 2D serving operators (r = 49), comma separated")
     ap.add_argument("--serve-requests", type=int, default=600, help="requests per rate of the default line's serving leg")
-    ap.add_argument("--no-legs", action="store_true", help="skip the serving and batched legs of the default line")
+    ap.add_argument("--no-legs", action="store_true", help="skip the 2D solve, serving and batched legs of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     choices=["bf_adjoint", "bf_forward", "hss_solve", "fio_solve", "bf2d_adjoint", "bf2d_forward"])
@@ -768,8 +833,10 @@ def main():
 
     legs = {}
     if rank == 0 and world == 1 and not args.no_legs:
+        legs["solve_2d"], op256 = c3_leg(max(3, args.steps // 2), args.warmup)
         legs["served_requests"] = serving_leg(args.serve_requests,
-                                              ops2d=tuple(int(x) for x in args.serve_2d.split(",") if x))
+                                              ops2d=tuple(int(x) for x in args.serve_2d.split(",") if x),
+                                              prebuilt={(256, 49): op256})
         legs["batched"] = batched_leg(max(3, args.steps // 2), args.warmup)
 
     cpu = None

@@ -104,7 +104,8 @@ typedef struct {
  * bf_build -- butterfly factorization K~ of K (Section 2.2, Eq. 2.1).
  *   n: points per dimension (power of two); d: dimension.
  *   d = 1: 16 <= n <= 2^24, r: Chebyshev interpolation rank (1..16), N = n.
- *   d = 2: 8 <= n <= 1024, r = 25 (5 x 5 tensor Chebyshev grid), N = n^2;
+ *   d = 2: 8 <= n <= 1024, r = r1^2 with 3 <= r1 <= 7 (r1 x r1 tensor
+ *     Chebyshev grid; the 2D workloads use r = 25), N = n^2;
  *     quadtrees, vectors in lexicographic order (x_i = (i1, i2)/n with
  *     i = i1 n + i2, xi_j = (j1 - n/2, j2 - n/2) with j = j1 n + j2).
  *   Trees: space/frequency trees of depth L = log2 n; middle level
@@ -126,6 +127,40 @@ fio_status bf_build(const fio_phase* phase, int n, int d, int r, void* stream, f
  *   sigma2 <= 0; otherwise as bf_build. */
 fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, void* stream,
                         fio_bf** out);
+
+/* bf_entries -- S sampled entries of K~ and of K (Section 2.2; the error
+ *   measure of Section 5).  rows, cols: host arrays of S indices in [0, N)
+ *   (lexicographic in 2D); 1 <= S <= 2^22.  Each K~ entry is evaluated in FP64
+ *   from the factor definitions of Eq. 2.1 (not from the stored complex64
+ *   tables): only one chain of pairs couples x_i with xi_j, so the entry is a
+ *   product of one r x r block per level.  K(i, j) = a(x_i, xi_j)
+ *   e^{2 pi i Phi(x_i, xi_j)} in FP64.  out: host array of 4 S doubles,
+ *   sample e at out[4e .. 4e+3] = (Re K~, Im K~, Re K, Im K).  A Hankel sample
+ *   at xi = 0 (amplitude infinite) is returned as zeros.  Synchronizes
+ *   `stream`.  Errors: FIO_EINVAL (null pointer, S or index out of range),
+ *   FIO_ENOMEM, FIO_ECUDA. */
+fio_status bf_entries(const fio_bf* bf, const int64_t* rows, const int64_t* cols, int S, void* stream, double* out);
+
+/* bf_entry_error -- e = sqrt(sum_e |K~_e - K_e|^2 / sum_e |K_e|^2) over the
+ *   samples, for the BF of rank r of (phase, amp, n, d) (amp may be NULL),
+ *   without building its tables; for a random sample this estimates the
+ *   relative error ||K~ - K|| / ||K|| in the Frobenius norm, the expected
+ *   value of the sampled-row error e_cBF of Section 5 for random vectors.
+ *   Arguments as bf_build_amp and bf_entries.  Errors: FIO_EINVAL (as
+ *   bf_build_amp; also when no sample has a finite nonzero K), FIO_ENOMEM,
+ *   FIO_ECUDA. */
+fio_status bf_entry_error(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, const int64_t* rows,
+                          const int64_t* cols, int S, void* stream, double* err);
+
+/* bf_build_tol -- adaptive BF rank (the BF tolerance of Section 5): the
+ *   smallest rank of the candidate list whose bf_entry_error on the given
+ *   samples is <= tol, then bf_build_amp at that rank.  Candidates: d = 1:
+ *   r = 4, 6, ..., 16; d = 2: r = r1^2, r1 = 3 .. 7.  If no candidate reaches
+ *   tol the largest is built and *err_out (> tol) says so.  *r_out, *err_out
+ *   (may be NULL): the rank built and its sampled error.  Errors: as
+ *   bf_build_amp and bf_entry_error; FIO_EINVAL for tol <= 0. */
+fio_status bf_build_tol(const fio_phase* phase, const fio_amp* amp, int n, int d, double tol, const int64_t* rows,
+                        const int64_t* cols, int S, void* stream, fio_bf** out, int* r_out, double* err_out);
 
 /* bf_apply -- Y = K~ X (adjoint = 0) or Y = K~^* X (adjoint = 1); the adjoint
  *   applies the conjugate-transposed factors in reverse order (Section 2.2).

@@ -52,6 +52,11 @@ SIGNATURES = {
     "bf_set_precision": (I32, [P, I32]),
     "bf_apply_noalloc": (I32, [P, P, P, I64, I32, I32, P]),
     "bf_free": (None, [P]),
+    "bf_entries": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), I32, P, ctypes.POINTER(ctypes.c_double)]),
+    "bf_entry_error": (I32, [ctypes.POINTER(Phase), ctypes.POINTER(Amp), I32, I32, I32, ctypes.POINTER(I64),
+                             ctypes.POINTER(I64), I32, P, ctypes.POINTER(ctypes.c_double)]),
+    "bf_build_tol": (I32, [ctypes.POINTER(Phase), ctypes.POINTER(Amp), I32, I32, ctypes.c_double, ctypes.POINTER(I64),
+                           ctypes.POINTER(I64), I32, P, PP, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
     "hss_build_from_samples": (I32, [ctypes.POINTER(Sampler), I64, I32, I32, ctypes.c_double, ctypes.c_uint64,
                                      P, PP]),
     "hss_from_generators": (I32, [I64, I32, ctypes.POINTER(I32), P, P, P, P, PP]),

@@ -33,6 +33,48 @@ def _block(x, n, name):
     return x.data_ptr(), (x.stride(0) if x.shape[0] > 1 else n), x.shape[0]
 
 
+def _dim(phase, d):
+    return (2 if phase in ("elliptic2d", "iso2d") else 1) if d is None else int(d)
+
+
+def _amp(amp):
+    """ctypes pointer to the amplitude (None: a = 1) and the array it borrows."""
+    import numpy as np
+    if amp is None:
+        return None, None
+    kind = amp if isinstance(amp, str) else amp[0]
+    a = _lib.Amp(_lib.AMP_KINDS[kind], 0, 1.0, None)
+    keep = None
+    if kind == "bumps":
+        keep = np.ascontiguousarray(np.asarray(amp[1], dtype=np.float64).reshape(-1, 2))
+        a.m, a.sigma2 = keep.shape[0], float(amp[2])
+        a.centers = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return ctypes.pointer(a), (a, keep)
+
+
+def _index_pair(rows, cols):
+    import numpy as np
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64).ravel())
+    c = np.ascontiguousarray(np.asarray(cols, dtype=np.int64).ravel())
+    if r.shape != c.shape:
+        raise ValueError("rows and cols must have the same length")
+    P = ctypes.POINTER(ctypes.c_int64)
+    return r.ctypes.data_as(P), c.ctypes.data_as(P), int(r.size), (r, c)
+
+
+def entry_error(n, r, rows, cols, phase="cabs", s=1.0, d=None, amp=None, stream=None):
+    """bf_entry_error: the FP64 relative error of the rank-r BF on the sampled entries, without
+    building its tables."""
+    d = _dim(phase, d)
+    ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
+    a, keep = _amp(amp)
+    pr, pc, S, kp = _index_pair(rows, cols)
+    e = ctypes.c_double()
+    check(lib.bf_entry_error(ctypes.byref(ph), a, int(n), d, int(r), pr, pc, S, _stream(stream), ctypes.byref(e)))
+    del keep, kp
+    return e.value
+
+
 class BF:
     """Butterfly factorization K~ of the FIO (bf_build / bf_apply).
 
@@ -41,29 +83,50 @@ class BF:
     and are held as (k, N) complex64 CUDA tensors; `self.n` is N.
     """
 
-    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None, d=None, amp=None):
+    def __init__(self, n, r=16, phase="cabs", s=1.0, stream=None, d=None, amp=None, _handle=None):
         """amp: None (a = 1), ("bumps", centers, sigma2) with centers an (m, 2) array of (x_k, xi_k)
         (Section 5.1), or "hankel" (Section 5.3, with phase "iso2d")."""
-        d = (2 if phase in ("elliptic2d", "iso2d") else 1) if d is None else int(d)
-        ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
-        h = ctypes.c_void_p()
-        if amp is None:
-            check(lib.bf_build(ctypes.byref(ph), int(n), d, int(r), _stream(stream), ctypes.byref(h)))
-        else:
-            import numpy as np
-            kind = amp if isinstance(amp, str) else amp[0]
-            a = _lib.Amp(_lib.AMP_KINDS[kind], 0, 1.0, None)
-            keep = None
-            if kind == "bumps":
-                keep = np.ascontiguousarray(np.asarray(amp[1], dtype=np.float64).reshape(-1, 2))
-                a.m, a.sigma2 = keep.shape[0], float(amp[2])
-                a.centers = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-            check(lib.bf_build_amp(ctypes.byref(ph), ctypes.byref(a), int(n), d, int(r), _stream(stream),
-                                   ctypes.byref(h)))
+        d = _dim(phase, d)
+        if _handle is None:
+            ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
+            a, keep = _amp(amp)
+            h = ctypes.c_void_p()
+            check(lib.bf_build_amp(ctypes.byref(ph), a, int(n), d, int(r), _stream(stream), ctypes.byref(h)))
             del keep
+        else:
+            h = _handle
         self._h = h
         self.n_side, self.d = int(n), d
         self.n, self.r, self.phase, self.s = int(n) ** d, int(r), phase, float(s)
+        self.entry_error = None
+
+    @classmethod
+    def with_tol(cls, n, tol, rows, cols, phase="cabs", s=1.0, d=None, amp=None, stream=None):
+        """Adaptive rank (bf_build_tol): the smallest candidate rank whose FP64 error on the sampled
+        entries (rows[e], cols[e]) is <= tol.  The handle's `r` and `entry_error` report the choice."""
+        d = _dim(phase, d)
+        ph = _lib.Phase(_lib.PHASE_KINDS[phase], float(s))
+        a, keep = _amp(amp)
+        pr, pc, S, kp = _index_pair(rows, cols)
+        h = ctypes.c_void_p()
+        r = ctypes.c_int()
+        e = ctypes.c_double()
+        check(lib.bf_build_tol(ctypes.byref(ph), a, int(n), d, float(tol), pr, pc, S, _stream(stream), ctypes.byref(h),
+                               ctypes.byref(r), ctypes.byref(e)))
+        del keep, kp
+        bf = cls(n, r.value, phase, s, d=d, _handle=h)
+        bf.entry_error = e.value
+        return bf
+
+    def entries(self, rows, cols, stream=None):
+        """(S, 2) complex128: column 0 the sampled entries of K~ evaluated in FP64 from the factor
+        definitions, column 1 the entries of K (bf_entries)."""
+        import numpy as np
+        pr, pc, S, kp = _index_pair(rows, cols)
+        out = np.empty(4 * S, dtype=np.float64)
+        check(lib.bf_entries(self._h, pr, pc, S, _stream(stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        del kp
+        return out.view(np.complex128).reshape(S, 2)
 
     @property
     def handle(self):

@@ -343,6 +343,119 @@ __global__ void k_quad(const float2* __restrict__ Sin, float2* __restrict__ Sout
     }
 }
 
+// ---------------------------------------------------------------- sampled entries (FP64)
+// e^{2 pi i ph} in FP64.
+__device__ __forceinline__ double2 expi2pi_d(double ph) {
+    const double fr = ph - rint(ph);
+    double sn, cs;
+    sincospi(2.0 * fr, &sn, &cs);
+    return make_double2(cs, sn);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// Lagrange polynomial l_k on the r Chebyshev points of a box, at the box coordinate v in [-1, 1].
+__device__ double lag_d(const Cheb& ch, int r, int k, double v) {
+    double p = 1.0;
+    for (int m = 0; m < r; ++m)
+        if (m != k) p *= (v - ch.t[m]) / (ch.t[k] - ch.t[m]);
+    return p;
+}
+
+// One sampled entry (x_i, xi_j) per thread: K~(i, j) in FP64 straight from the factor entries of
+// Eq. 2.1 (the interpolation functions of Section 2.2, not the stored FP32 tables) and the exact
+// K(i, j) = a(x_i, xi_j) e^{2 pi i Phi(x_i, xi_j)}.  Only one chain of pairs couples x_i with
+// xi_j -- at space level s the pair (tau = the box of level s holding x_i, sigma = the box of
+// frequency level L - s holding xi_j) -- so the entry is a product of one r x r block per level:
+// r coefficients carried from V through C, M and B to U.
+__global__ void k_entry_chain(const int64_t* __restrict__ rows, const int64_t* __restrict__ cols, int S, PhaseDev ph,
+                              AmpDev amp, Cheb ch, int n, int L, int h, int sU, int sV, int r, double2* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S) return;
+    const int64_t i = rows[e], j = cols[e];
+    const double x = double(i) / n, xi = double(j) - 0.5 * n;
+    double2 c[kMaxR], d[kMaxR];
+    auto fhalf = [&](int l) { return ldexp(double(n), -l - 1); };   // half width of a frequency box of level l
+    {   // V at space level sV: c_t = e^{2 pi i (Phi(y, xi) - Phi(y, gamma_t))} q_t(xi)
+        const int64_t tau = i >> (L - sV), sg = j >> sV;
+        const int l = L - sV;
+        const double y = space_center(sV, tau), fc = freq_center(n, l, sg);
+        for (int t = 0; t < r; ++t) {
+            const double g = freq_node(ch, n, l, sg, t);
+            const double2 w = expi2pi_d(phi(ph, y, xi) - phi(ph, y, g));
+            const double q = lag_d(ch, r, t, (xi - fc) / fhalf(l));
+            c[t] = make_double2(w.x * q, w.y * q);
+        }
+    }
+    for (int s = sV; s < h; ++s) {   // C, pair level s -> s+1
+        const int64_t tau1 = i >> (L - s - 1), sg1 = j >> (s + 1), beta = j >> s;
+        const double y1 = space_center(s + 1, tau1), fc1 = freq_center(n, L - s - 1, sg1);
+        for (int jj = 0; jj < r; ++jj) {
+            const double gj = freq_node(ch, n, L - s - 1, sg1, jj);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < r; ++t) {
+                const double gb = freq_node(ch, n, L - s, beta, t);
+                const double2 w = expi2pi_d(phi(ph, y1, gb) - phi(ph, y1, gj));
+                const double q = lag_d(ch, r, jj, (gb - fc1) / fhalf(L - s - 1));
+                const double2 v = zmul(w, c[t]);
+                acc.x += q * v.x;
+                acc.y += q * v.y;
+            }
+            d[jj] = acc;
+        }
+        for (int t = 0; t < r; ++t) c[t] = d[t];
+    }
+    {   // M at level h: d_i = sum_j a(z_i, gamma_j) e^{2 pi i Phi(z_i, gamma_j)} c_j
+        const int64_t tau = i >> (L - h), sg = j >> h;
+        for (int ii = 0; ii < r; ++ii) {
+            const double z = space_node(ch, h, tau, ii);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < r; ++t) {
+                const double g = freq_node(ch, n, L - h, sg, t);
+                const double2 w = zmul(expi2pi_d(phi(ph, z, g)), c[t]);
+                const double a = amp1d(amp, z, g);
+                acc.x += a * w.x;
+                acc.y += a * w.y;
+            }
+            d[ii] = acc;
+        }
+    }
+    for (int s = h; s < sU; ++s) {   // B, pair level s -> s+1
+        const int64_t al = i >> (L - s), tau1 = i >> (L - s - 1), beta = j >> s;
+        const double eta = freq_center(n, L - s, beta), ya = space_center(s, al);
+        for (int ii = 0; ii < r; ++ii) {
+            const double z = space_node(ch, s + 1, tau1, ii);
+            const double pz = ldexp(1.0, s + 1) * (z - ya);   // coordinate of z in the box of alpha
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < r; ++t) {
+                const double za = space_node(ch, s, al, t);
+                const double2 w = zmul(expi2pi_d(phi(ph, z, eta) - phi(ph, za, eta)), d[t]);
+                const double p = lag_d(ch, r, t, pz);
+                acc.x += p * w.x;
+                acc.y += p * w.y;
+            }
+            c[ii] = acc;
+        }
+        for (int t = 0; t < r; ++t) d[t] = c[t];
+    }
+    double2 y = make_double2(0.0, 0.0);
+    {   // U at space level sU: y = sum_i e^{2 pi i (Phi(x, eta) - Phi(z_i, eta))} p_i(x) d_i
+        const int64_t tau = i >> (L - sU), sg = j >> sU;
+        const double eta = freq_center(n, L - sU, sg), px = ldexp(1.0, sU + 1) * (x - space_center(sU, tau));
+        for (int t = 0; t < r; ++t) {
+            const double z = space_node(ch, sU, tau, t);
+            const double2 w = zmul(expi2pi_d(phi(ph, x, eta) - phi(ph, z, eta)), d[t]);
+            const double p = lag_d(ch, r, t, px);
+            y.x += p * w.x;
+            y.y += p * w.y;
+        }
+    }
+    const double2 k = expi2pi_d(phi(ph, x, xi));
+    const double a = amp1d(amp, x, xi);
+    out[2 * e] = y;
+    out[2 * e + 1] = make_double2(a * k.x, a * k.y);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host helpers
@@ -396,6 +509,20 @@ fio_status bf_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t l
     return FIO_OK;
 }
 
+// Sampled entries of a 1D BF of rank r (K~ then K per sample, device double2[2 S]).
+fio_status bf1d_entries(const fio_phase& phase, const AmpDev& amp, int n, int r, const int64_t* rows,
+                        const int64_t* cols, int S, double2* out, cudaStream_t st) {
+    const int L = ilog2_exact(n);
+    const int h = L / 2, sU = std::max(L - 3, h), sV = std::min(3, h);
+    Cheb ch{};
+    for (int k = 0; k < r; ++k) ch.t[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * r));
+    const PhaseDev ph{phase.kind, phase.s};
+    FIO_LAUNCH("k_entry_chain", st,
+               (k_entry_chain<<<cdiv(S, 64), 64, 0, st>>>(rows, cols, S, ph, amp, ch, n, L, h, sU, sV, r, out)));
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
 }  // namespace fio
 
 using namespace fio;
@@ -404,11 +531,9 @@ extern "C" fio_status bf_build(const fio_phase* phase, int n, int d, int r, void
     return bf_build_amp(phase, nullptr, n, d, r, stream, out);
 }
 
-extern "C" fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, void* stream,
-                                   fio_bf** out) {
-    if (!out || !phase) return fail(FIO_EINVAL, "bf_build: null pointer");
-    *out = nullptr;
-    AmpDev ad;
+// The device form of an amplitude, checked against the dimension and phase it is used with.
+static fio_status amp_dev(const fio_phase* phase, const fio_amp* amp, int n, int d, AmpDev& ad) {
+    ad = AmpDev{};
     if (amp && amp->kind != FIO_AMP_ONE) {
         if (amp->kind == FIO_AMP_BUMPS) {
             if (d != 1) return fail(FIO_EINVAL, "bf_build_amp: the Gaussian-bump amplitude is 1D");
@@ -427,10 +552,22 @@ extern "C" fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, i
             return fail(FIO_EINVAL, "bf_build_amp: unknown amplitude kind");
         }
     }
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_build_amp(const fio_phase* phase, const fio_amp* amp, int n, int d, int r, void* stream,
+                                   fio_bf** out) {
+    if (!out || !phase) return fail(FIO_EINVAL, "bf_build: null pointer");
+    *out = nullptr;
+    AmpDev ad;
+    FIO_TRY(amp_dev(phase, amp, n, d, ad));
     if (d == 2) {
         const int L2 = ilog2_exact(n);
         if (L2 < 3 || L2 > 10) return fail(FIO_EINVAL, "bf_build: 2D needs n a power of two in [8, 1024]");
-        if (r != 25) return fail(FIO_EINVAL, "bf_build: 2D needs r = 25 (5 x 5 tensor Chebyshev grid)");
+        int r1 = 1;
+        while ((r1 + 1) * (r1 + 1) <= r) ++r1;
+        if (r1 * r1 != r || !bf2d_ok_r1(r1))
+            return fail(FIO_EINVAL, "bf_build: 2D needs r = r1^2 with 3 <= r1 <= 7 (r1 x r1 tensor Chebyshev grid)");
         if (!bf2d_ok_kind(phase->kind)) return fail(FIO_EINVAL, "bf_build: 2D phase must be DFT, 2D elliptic or 2D iso");
         fio_bf* bf = new fio_bf();
         bf->phase = *phase;
@@ -566,6 +703,128 @@ fio_status bf_apply_prec(const fio_bf* bfc, const float2* X, float2* Y, int64_t 
     return FIO_OK;
 }
 }  // namespace fio
+
+// ---------------------------------------------------------------- sampled entries, adaptive rank
+namespace {
+// Entries (rows[e], cols[e]) of the BF of rank r (FP64 chain) and of K, to the host.
+fio_status entries_host(const fio_phase& phase, const AmpDev& ad, int nside, int d, int r, const int64_t* rows,
+                        const int64_t* cols, int S, cudaStream_t st, std::vector<double2>& out) {
+    if (!rows || !cols) return fail(FIO_EINVAL, "bf_entries: null index array");
+    if (S < 1 || S > (1 << 22)) return fail(FIO_EINVAL, "bf_entries: need 1 <= S <= 2^22 samples");
+    const int64_t N = d == 2 ? int64_t(nside) * nside : int64_t(nside);
+    for (int e = 0; e < S; ++e)
+        if (rows[e] < 0 || rows[e] >= N || cols[e] < 0 || cols[e] >= N)
+            return fail(FIO_EINVAL, "bf_entries: index out of range");
+    DevBuf buf;
+    fio_status s = buf.ensure(size_t(S) * (2 * sizeof(int64_t) + 2 * sizeof(double2)));
+    if (s != FIO_OK) return s;
+    int64_t* drows = buf.as<int64_t>();
+    int64_t* dcols = drows + S;
+    double2* dout = reinterpret_cast<double2*>(dcols + S);
+    out.assign(size_t(2) * S, make_double2(0.0, 0.0));
+    cudaError_t e = cudaMemcpyAsync(drows, rows, size_t(S) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dcols, cols, size_t(S) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        buf.release();
+        return cuda_status(e, "bf_entries: index copy");
+    }
+    if (d == 2) {
+        int r1 = 1;
+        while ((r1 + 1) * (r1 + 1) <= r) ++r1;
+        s = bf2d_entries(phase, ad.kind, nside, r1, drows, dcols, S, dout, st);
+    } else {
+        s = bf1d_entries(phase, ad, nside, r, drows, dcols, S, dout, st);
+    }
+    if (s == FIO_OK) {
+        e = cudaMemcpyAsync(out.data(), dout, size_t(2) * S * sizeof(double2), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "bf_entries");
+    }
+    buf.release();
+    return s;
+}
+
+// sqrt(sum |K~ - K|^2 / sum |K|^2) over the samples
+fio_status entry_error(const std::vector<double2>& v, double* err) {
+    double num = 0.0, den = 0.0;
+    for (size_t e = 0; e + 1 < v.size(); e += 2) {
+        const double dr = v[e].x - v[e + 1].x, di = v[e].y - v[e + 1].y;
+        num += dr * dr + di * di;
+        den += v[e + 1].x * v[e + 1].x + v[e + 1].y * v[e + 1].y;
+    }
+    if (!(den > 0.0)) return fail(FIO_EINVAL, "bf_entry_error: no sample with a finite nonzero entry of K");
+    *err = std::sqrt(num / den);
+    return FIO_OK;
+}
+
+fio_status check_geometry(const fio_phase* phase, int n, int d, int r) {
+    if (!phase) return fail(FIO_EINVAL, "null phase");
+    if (d == 2) {
+        const int L2 = ilog2_exact(n);
+        int r1 = 1;
+        while ((r1 + 1) * (r1 + 1) <= r) ++r1;
+        if (L2 < 3 || L2 > 10 || r1 * r1 != r || !bf2d_ok_r1(r1) || !bf2d_ok_kind(phase->kind))
+            return fail(FIO_EINVAL, "2D needs n = 2^3..2^10, r = r1^2 with 3 <= r1 <= 7 and a 2D phase");
+        return FIO_OK;
+    }
+    if (d != 1) return fail(FIO_EINVAL, "d must be 1 or 2");
+    const int L = ilog2_exact(n);
+    if (L < 4 || L > 24 || r < 1 || r > kMaxR) return fail(FIO_EINVAL, "1D needs n = 2^4..2^24 and 1 <= r <= 16");
+    if (phase->kind != FIO_PHASE_DFT && phase->kind != FIO_PHASE_1D_CABS && phase->kind != FIO_PHASE_1D_CABS8)
+        return fail(FIO_EINVAL, "1D needs a 1D phase");
+    return FIO_OK;
+}
+}  // namespace
+
+extern "C" fio_status bf_entries(const fio_bf* bf, const int64_t* rows, const int64_t* cols, int S, void* stream,
+                                 double* out) {
+    if (!bf || !out) return fail(FIO_EINVAL, "bf_entries: null pointer");
+    std::vector<double2> v;
+    FIO_TRY(entries_host(bf->phase, bf->amp, bf->nside, bf->d, bf->r, rows, cols, S, as_stream(stream), v));
+    std::memcpy(out, v.data(), v.size() * sizeof(double2));
+    return FIO_OK;
+}
+
+extern "C" fio_status bf_entry_error(const fio_phase* phase, const fio_amp* amp, int n, int d, int r,
+                                     const int64_t* rows, const int64_t* cols, int S, void* stream, double* err) {
+    if (!err) return fail(FIO_EINVAL, "bf_entry_error: null pointer");
+    FIO_TRY(check_geometry(phase, n, d, r));
+    AmpDev ad;
+    FIO_TRY(amp_dev(phase, amp, n, d, ad));
+    std::vector<double2> v;
+    FIO_TRY(entries_host(*phase, ad, n, d, r, rows, cols, S, as_stream(stream), v));
+    return entry_error(v, err);
+}
+
+extern "C" fio_status bf_build_tol(const fio_phase* phase, const fio_amp* amp, int n, int d, double tol,
+                                   const int64_t* rows, const int64_t* cols, int S, void* stream, fio_bf** out,
+                                   int* r_out, double* err_out) {
+    if (!out || !phase) return fail(FIO_EINVAL, "bf_build_tol: null pointer");
+    *out = nullptr;
+    if (!(tol > 0.0)) return fail(FIO_EINVAL, "bf_build_tol: tol must be positive");
+    std::vector<int> cand;
+    if (d == 2)
+        for (int r1 = 3; r1 <= 7; ++r1) cand.push_back(r1 * r1);
+    else
+        for (int r = 4; r <= kMaxR; r += 2) cand.push_back(r);
+    AmpDev ad;
+    FIO_TRY(amp_dev(phase, amp, n, d, ad));
+    int r_pick = cand.back();
+    double e_pick = 0.0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        FIO_TRY(check_geometry(phase, n, d, cand[c]));
+        std::vector<double2> v;
+        FIO_TRY(entries_host(*phase, ad, n, d, cand[c], rows, cols, S, as_stream(stream), v));
+        double e = 0.0;
+        FIO_TRY(entry_error(v, &e));
+        r_pick = cand[c];
+        e_pick = e;
+        if (e <= tol) break;
+    }
+    if (r_out) *r_out = r_pick;
+    if (err_out) *err_out = e_pick;
+    return bf_build_amp(phase, amp, n, d, r_pick, stream, out);
+}
 
 extern "C" fio_status bf_apply(fio_bf* bf, const void* X, void* Y, int64_t ld, int k, int adjoint, void* stream) {
     return bf_apply_prec(bf, static_cast<const float2*>(X), static_cast<float2*>(Y), ld, k, adjoint, -1,

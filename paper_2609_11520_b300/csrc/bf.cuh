@@ -97,10 +97,18 @@ double lagrange_host(const double* t, int r, int k, double u);
 // 2D handles (d = 2, r = 25; bf2d.cu).  The same fio_bf fields hold the 2D
 // tables: VP, UP, M, C (F_s), B (E_s) and P (Pc | Pc^T | QV | QU).
 bool bf2d_ok_kind(int kind);
+bool bf2d_ok_r1(int r1);
 fio_status bf2d_build(fio_bf* bf, cudaStream_t st);
 fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool morton,
                            float2* s0, float2* s1, cudaStream_t st);
 fio_status bf2d_unmorton(const fio_bf* bf, const float2* Xm, float2* X, int64_t ld, int k, cudaStream_t st);
+// Sampled entries (rows[e], cols[e]) of a BF of the given rank, evaluated in FP64 from the factor
+// definitions, and of K itself: out[2 e] = K~, out[2 e + 1] = K (device arrays).  1D: rank r;
+// 2D: r1 x r1 grid, lexicographic indices.
+fio_status bf1d_entries(const fio_phase& phase, const AmpDev& amp, int n, int r, const int64_t* rows,
+                        const int64_t* cols, int S, double2* out, cudaStream_t st);
+fio_status bf2d_entries(const fio_phase& phase, int amp_kind, int n, int r1, const int64_t* rows, const int64_t* cols,
+                        int S, double2* out, cudaStream_t st);
 // bf_apply with the frequency vectors of a 2D handle in quadtree (Morton)
 // order when `morton` is set (the order of the HSS of K~^* K~); 1D: bf_apply.
 fio_status bf_apply_ord(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int k, int adjoint, bool morton,

@@ -1,6 +1,6 @@
 // Butterfly factorization of a 2D FIO (Section 2.2 with d = 2, Section 5.2):
-// quadtree boxes, tensor Chebyshev grids of r1 x r1 = 25 nodes, the same
-// factor sequence as Eq. 2.1.
+// quadtree boxes, tensor Chebyshev grids of r1 x r1 nodes (r1 = 3 .. 7; the
+// kernels are instantiated per r1), the same factor sequence as Eq. 2.1.
 //
 // Geometry (per dimension as in 1D).  n points per dimension, N = n^2,
 // L = log2 n, h = floor(L/2), sU = max(L-3, h), sV = min(3, h).  A box at
@@ -35,14 +35,24 @@
 namespace fio {
 namespace {
 
-constexpr int R1 = 5;
-constexpr int R = R1 * R1;      // 25
-constexpr int RP = 28;          // padded row of a real 25-vector (seven float4)
 constexpr int TB = 256;
-constexpr int kPhGroups = 8;    // transfer groups whose phase rows a CTA stages in shared memory
+constexpr int kMinR1 = 3, kMaxR1 = 7;
 
-struct Cheb5 {
-    double t[R1];
+// Per-grid constants: R = r1^2 coefficients per pair, RP = R padded to whole float4 rows, PHG
+// transfer groups whose phase rows a CTA stages in shared memory, MP middle-level pairs per CTA
+// (the static shared memory of the transfer kernel and the M block of the middle kernel shrink
+// with R so that r1 = 7 still fits).
+template <int R1>
+struct G2 {
+    static constexpr int R = R1 * R1;
+    static constexpr int RP = (R + 3) / 4 * 4;
+    static constexpr int PHG = R <= 25 ? 8 : (R <= 36 ? 2 : 1);
+    static constexpr int MP = R <= 36 ? 16 : 8;
+};
+
+// first-kind Chebyshev points on [-1, 1] of the handle's r1
+struct Cheb2 {
+    double t[kMaxR1];
 };
 
 // Nonlinear part Phi(x, xi) - x . xi of the 2D families (Sections 5.2 and 5.3; 0 for the DFT).
@@ -91,14 +101,14 @@ __device__ __forceinline__ double sctr(int s, int64_t a, int d) {
     const int64_t ad = d == 0 ? (a >> s) : (a & ((int64_t(1) << s) - 1));
     return ldexp(double(ad) + 0.5, -s);
 }
-__device__ __forceinline__ double snode(const Cheb5& ch, int s, int64_t a, int d, int k) {
+__device__ __forceinline__ double snode(const Cheb2& ch, int s, int64_t a, int d, int k) {
     return sctr(s, a, d) + ldexp(0.5, -s) * ch.t[k];
 }
 __device__ __forceinline__ double fctr(int n, int l, int64_t b, int d) {
     const int64_t bd = d == 0 ? (b >> l) : (b & ((int64_t(1) << l) - 1));
     return -0.5 * n + (double(bd) + 0.5) * ldexp(double(n), -l);
 }
-__device__ __forceinline__ double fnode(const Cheb5& ch, int n, int l, int64_t b, int d, int k) {
+__device__ __forceinline__ double fnode(const Cheb2& ch, int n, int l, int64_t b, int d, int k) {
     return fctr(n, l, b, d) + ldexp(double(n), -l - 1) * ch.t[k];
 }
 
@@ -122,7 +132,9 @@ __global__ void k2_tab_VP(float2* VP, Ph2 kind, int n, int sV) {
 }
 
 // groups g = tau 4^(L-s-1) + sigma', entries [g][o][c][t]
-__global__ void k2_tab_F(float2* F, Ph2 kind, Cheb5 ch, int n, int L, int s) {
+template <int R1>
+__global__ void k2_tab_F(float2* F, Ph2 kind, Cheb2 ch, int n, int L, int s) {
+    constexpr int R = G2<R1>::R;
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N / 4 * 16 * R) return;
@@ -138,7 +150,9 @@ __global__ void k2_tab_F(float2* F, Ph2 kind, Cheb5 ch, int n, int L, int s) {
                 phi2(kind, sctr(s, tau, 0), sctr(s, tau, 1), g1, g2));
 }
 
-__global__ void k2_tab_M(float2* M, Ph2 kind, int amp_kind, Cheb5 ch, int n, int L, int h) {
+template <int R1>
+__global__ void k2_tab_M(float2* M, Ph2 kind, int amp_kind, Cheb2 ch, int n, int L, int h) {
+    constexpr int R = G2<R1>::R;
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N * R * R) return;
@@ -154,7 +168,9 @@ __global__ void k2_tab_M(float2* M, Ph2 kind, int amp_kind, Cheb5 ch, int n, int
     M[e] = amp_kind == FIO_AMP_HANKEL ? cmul(hankel_amp(phi2_nl(kind.kind, kind.s, z1, z2, g1, g2)), m) : m;
 }
 
-__global__ void k2_tab_E(float2* E, Ph2 kind, Cheb5 ch, int n, int L, int s) {
+template <int R1>
+__global__ void k2_tab_E(float2* E, Ph2 kind, Cheb2 ch, int n, int L, int s) {
+    constexpr int R = G2<R1>::R;
     const int64_t N = int64_t(n) * n;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N / 4 * 16 * R) return;
@@ -181,30 +197,36 @@ __global__ void k2_tab_UP(float2* UP, Ph2 kind, int n, int L, int sU) {
 
 // ---------------------------------------------------------------- apply
 // Column block: X, Y (N x kc, ld); coefficient states S[col][pair][t] with
-// SN = N * 25 complex per column.
+// SN = N * R complex per column.
 
-// 25-term real-by-complex dot product of a padded smem row with a register vector.
+// R-term real-by-complex dot product of a padded smem row with a register vector.
+template <int R>
 __device__ __forceinline__ float2 rowdot(const float* __restrict__ row, const float2 (&x)[R]) {
     const float4* r4 = reinterpret_cast<const float4*>(row);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < R / 4; ++q) {
         const float4 a = r4[q];
         acc.x = fmaf(a.x, x[4 * q].x, acc.x); acc.y = fmaf(a.x, x[4 * q].y, acc.y);
         acc.x = fmaf(a.y, x[4 * q + 1].x, acc.x); acc.y = fmaf(a.y, x[4 * q + 1].y, acc.y);
         acc.x = fmaf(a.z, x[4 * q + 2].x, acc.x); acc.y = fmaf(a.z, x[4 * q + 2].y, acc.y);
         acc.x = fmaf(a.w, x[4 * q + 3].x, acc.x); acc.y = fmaf(a.w, x[4 * q + 3].y, acc.y);
     }
-    const float a24 = row[24];
-    acc.x = fmaf(a24, x[24].x, acc.x); acc.y = fmaf(a24, x[24].y, acc.y);
+#pragma unroll
+    for (int t = R / 4 * 4; t < R; ++t) {
+        acc.x = fmaf(row[t], x[t].x, acc.x);
+        acc.y = fmaf(row[t], x[t].y, acc.y);
+    }
     return acc;
 }
 
 // V (forward): c(a, b, t) = sum_q QV[t][q] VP[a][xi(b, q)] f(xi(b, q)).
 // CTA: one frequency leaf b, 4 columns; thread (a, column).
+template <int R1>
 __global__ void __launch_bounds__(TB) k2_V_fwd(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S,
                                                int64_t SN, const float2* __restrict__ VP, const float* __restrict__ QV,
                                                int n, int L, int sV, int kc, int mort) {
+    constexpr int R = G2<R1>::R;
     __shared__ float2 vps[64][65];
     __shared__ float2 fs[4][64];
     __shared__ float qv[R][64];
@@ -242,9 +264,11 @@ __global__ void __launch_bounds__(TB) k2_V_fwd(const float2* __restrict__ X, int
 }
 
 // V^*: f(xi(b, q)) = sum_a conj(VP[a][xi]) sum_t QV[t][q] c(a, b, t).  Thread (q, column).
+template <int R1>
 __global__ void __launch_bounds__(TB) k2_V_adj(const float2* __restrict__ S, int64_t SN, float2* __restrict__ Y,
                                                int64_t ld, const float2* __restrict__ VP, const float* __restrict__ QV,
                                                int n, int L, int sV, int kc, int mort) {
+    constexpr int R = G2<R1>::R;
     extern __shared__ float4 smem_v[];
     float2(*vps)[65] = reinterpret_cast<float2(*)[65]>(smem_v);                 // [64][65]
     float2* cs = reinterpret_cast<float2*>(smem_v) + 64 * 65;                     // [4][64][R]
@@ -292,10 +316,11 @@ __global__ void __launch_bounds__(TB) k2_V_adj(const float2* __restrict__ S, int
 //   MS: out[u][v] = sum_w Ph[u,w,v] sum_t A_u[v][t] x[w][t]            A = Pc^T
 // Ph[u,w,.] = table[g][o][c][.] (conjugated for the adjoint).
 // Thread (group, column, u); 64 (group, column) items per CTA.
-template <bool SM, bool ADJ>
-__global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin, float2* __restrict__ Sout, int64_t SN,
+template <int R1, bool SM, bool ADJ>
+__global__ void __launch_bounds__(TB, R1 <= 5 ? 2 : 1) k2_trans(const float2* __restrict__ Sin, float2* __restrict__ Sout, int64_t SN,
                                                   const float2* __restrict__ Ph, const float* __restrict__ Am, int L,
                                                   int s, int kc) {
+    constexpr int R = G2<R1>::R, RP = G2<R1>::RP, kPhGroups = G2<R1>::PHG;
     __shared__ __align__(16) float A[4 * R * RP];
     __shared__ float2 phs[kPhGroups * 16 * R];   // phase rows of the CTA's groups (when they fit)
     for (int i = threadIdx.x; i < 4 * R * RP; i += TB) A[i] = Am[i];
@@ -335,12 +360,12 @@ __global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin
             for (int t = 0; t < R; ++t) xv[t] = ADJ ? cmulc(phv(t), xv[t]) : cmul(phv(t), xv[t]);
             const float* Aw = A + w * R * RP;
 #pragma unroll
-            for (int v = 0; v < R; ++v) acc[v] = cadd(acc[v], rowdot(Aw + v * RP, xv));
+            for (int v = 0; v < R; ++v) acc[v] = cadd(acc[v], rowdot<R>(Aw + v * RP, xv));
         } else {
             const float* Au = A + u * R * RP;
 #pragma unroll
             for (int v = 0; v < R; ++v) {
-                const float2 tmp = rowdot(Au + v * RP, xv);
+                const float2 tmp = rowdot<R>(Au + v * RP, xv);
                 if (ADJ) cfmac(acc[v], phv(v), tmp);
                 else cfma(acc[v], phv(v), tmp);
             }
@@ -352,20 +377,21 @@ __global__ void __launch_bounds__(TB, 2) k2_trans(const float2* __restrict__ Sin
 }
 
 // Middle level: y[i] = sum_j M[p][i][j] x[j] (adjoint: x[j] = sum_i conj(M[p][i][j]) y[i]).
-// CTA: 16 pairs x 16 columns; thread (pair, column).
-template <bool ADJ>
+// CTA: MP pairs x TB / MP columns; thread (pair, column).
+template <int R1, bool ADJ>
 __global__ void __launch_bounds__(TB) k2_M(const float2* __restrict__ Sin, float2* __restrict__ Sout, int64_t SN,
                                            const float2* __restrict__ M, int64_t npairs, int kc) {
+    constexpr int R = G2<R1>::R, MP = G2<R1>::MP, CPB = TB / MP;
     extern __shared__ float4 smem_m[];
-    float2* Ms = reinterpret_cast<float2*>(smem_m);   // [16][R*R]
-    const int64_t p0 = int64_t(blockIdx.x) * 16;
-    const int np = int(std::min<int64_t>(16, npairs - p0));
+    float2* Ms = reinterpret_cast<float2*>(smem_m);   // [MP][R*R]
+    const int64_t p0 = int64_t(blockIdx.x) * MP;
+    const int np = int(std::min<int64_t>(MP, npairs - p0));
     const float4* src = reinterpret_cast<const float4*>(M + p0 * R * R);
     float4* dst = reinterpret_cast<float4*>(Ms);
-    for (int i = threadIdx.x; i < np * R * R / 2; i += TB) dst[i] = src[i];   // R*R*16 B per pair: even count of float4
+    for (int i = threadIdx.x; i < np * R * R / 2; i += TB) dst[i] = src[i];   // p0 even: 16-byte aligned
     if (np * R * R % 2) Ms[np * R * R - 1] = M[(p0 + np) * R * R - 1];
     __syncthreads();
-    const int pl = threadIdx.x >> 4, col = blockIdx.y * 16 + (threadIdx.x & 15);
+    const int pl = threadIdx.x / CPB, col = blockIdx.y * CPB + threadIdx.x % CPB;
     if (pl >= np || col >= kc) return;
     const float2* m = Ms + pl * R * R;
     const float2* x = Sin + col * SN + (p0 + pl) * R;
@@ -389,9 +415,11 @@ __global__ void __launch_bounds__(TB) k2_M(const float2* __restrict__ Sin, float
 
 // U (forward): y(x) = sum_b UP[x][b] sum_i QU[x_loc][i] d(tau, b, i).
 // CTA: one space leaf tau, 4 columns; thread (x_loc, column).
+template <int R1>
 __global__ void __launch_bounds__(TB) k2_U_fwd(const float2* __restrict__ S, int64_t SN, float2* __restrict__ Y,
                                                int64_t ld, const float2* __restrict__ UP, const float* __restrict__ QU,
                                                int n, int L, int sU, int kc) {
+    constexpr int R = G2<R1>::R;
     extern __shared__ float4 smem_u[];
     float2(*ups)[65] = reinterpret_cast<float2(*)[65]>(smem_u);
     float2* ds = reinterpret_cast<float2*>(smem_u) + 64 * 65;      // [4][64][R]
@@ -428,9 +456,11 @@ __global__ void __launch_bounds__(TB) k2_U_fwd(const float2* __restrict__ S, int
 }
 
 // U^*: d(tau, b, i) = sum_x QU[x_loc][i] conj(UP[x][b]) g(x).  Thread (b, column).
+template <int R1>
 __global__ void __launch_bounds__(TB) k2_U_adj(const float2* __restrict__ X, int64_t ld, float2* __restrict__ S,
                                                int64_t SN, const float2* __restrict__ UP, const float* __restrict__ QU,
                                                int n, int L, int sU, int kc) {
+    constexpr int R = G2<R1>::R;
     __shared__ float2 ups[64][65];
     __shared__ float2 gs[4][64];
     __shared__ float qu[64 * R];
@@ -464,6 +494,137 @@ __global__ void __launch_bounds__(TB) k2_U_adj(const float2* __restrict__ X, int
     for (int i = 0; i < R; ++i) out[i] = acc[i];
 }
 
+// ---------------------------------------------------------------- sampled entries (FP64)
+__device__ __forceinline__ double2 expi_d(double ph) {
+    const double fr = ph - rint(ph);
+    double sn, cs;
+    sincospi(2.0 * fr, &sn, &cs);
+    return make_double2(cs, sn);
+}
+__device__ __forceinline__ double2 zmul2(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// 1D Lagrange polynomial l_k on the r1 Chebyshev points, at the box coordinate v in [-1, 1]
+__device__ double lag1_d(const Cheb2& ch, int r1, int k, double v) {
+    double p = 1.0;
+    for (int m = 0; m < r1; ++m)
+        if (m != k) p *= (v - ch.t[m]) / (ch.t[k] - ch.t[m]);
+    return p;
+}
+// the Hankel amplitude of Section 5.3 in FP64
+__device__ __forceinline__ double2 hankel_amp_d(double ph) {
+    const double z = 2.0 * M_PI * ph;
+    const double2 w = expi_d(-ph);
+    return zmul2(make_double2(j0(z), y0(z)), w);
+}
+// box of space level s holding the point (i1, i2) / n, and of frequency level l holding (j1, j2)
+__device__ __forceinline__ int64_t box_at(int64_t i1, int64_t i2, int L, int s) {
+    return ((i1 >> (L - s)) << s) + (i2 >> (L - s));
+}
+
+// One sampled entry per thread, as the 1D k_entry_chain: K~(i, j) in FP64 from the factor entries
+// (tensor Chebyshev grids of r1 x r1 points, four children per box) along the single chain of pairs
+// (box of space level s holding x_i, box of frequency level L - s holding xi_j), and the exact K(i, j).
+// A Hankel sample at xi = 0 (where the amplitude is infinite) is written as zeros.
+template <int R1>
+__global__ void k2_entry_chain(const int64_t* __restrict__ rows, const int64_t* __restrict__ cols, int S, Ph2 kind,
+                               int amp_kind, Cheb2 ch, int n, int L, int h, int sU, int sV, double2* __restrict__ out) {
+    constexpr int R = G2<R1>::R;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S) return;
+    const int64_t i = rows[e], j = cols[e];
+    const int64_t i1 = i / n, i2 = i % n, j1 = j / n, j2 = j % n;
+    const double x1 = double(i1) / n, x2 = double(i2) / n, k1 = double(j1) - 0.5 * n, k2 = double(j2) - 0.5 * n;
+    if (amp_kind == FIO_AMP_HANKEL && k1 == 0.0 && k2 == 0.0) {
+        out[2 * e] = out[2 * e + 1] = make_double2(0.0, 0.0);
+        return;
+    }
+    double2 c[R], d[R];
+    auto fhalf = [&](int l) { return ldexp(double(n), -l - 1); };
+    auto amp = [&](double a1, double a2, double b1, double b2) {
+        return amp_kind == FIO_AMP_HANKEL ? hankel_amp_d(phi2_nl(kind.kind, kind.s, a1, a2, b1, b2)) : make_double2(1.0, 0.0);
+    };
+    {   // V at space level sV
+        const int l = L - sV;
+        const int64_t tau = box_at(i1, i2, L, sV), sg = box_at(j1, j2, L, l);
+        const double y1 = sctr(sV, tau, 0), y2 = sctr(sV, tau, 1);
+        const double v1 = (k1 - fctr(n, l, sg, 0)) / fhalf(l), v2 = (k2 - fctr(n, l, sg, 1)) / fhalf(l);
+        for (int t = 0; t < R; ++t) {
+            const double g1 = fnode(ch, n, l, sg, 0, t / R1), g2 = fnode(ch, n, l, sg, 1, t % R1);
+            const double2 w = expi_d(phi2(kind, y1, y2, k1, k2) - phi2(kind, y1, y2, g1, g2));
+            const double q = lag1_d(ch, R1, t / R1, v1) * lag1_d(ch, R1, t % R1, v2);
+            c[t] = make_double2(w.x * q, w.y * q);
+        }
+    }
+    for (int s = sV; s < h; ++s) {   // C, pair level s -> s+1
+        const int l1 = L - s - 1;
+        const int64_t tau1 = box_at(i1, i2, L, s + 1), sg1 = box_at(j1, j2, L, l1), beta = box_at(j1, j2, L, L - s);
+        const double y1 = sctr(s + 1, tau1, 0), y2 = sctr(s + 1, tau1, 1);
+        const double f1 = fctr(n, l1, sg1, 0), f2 = fctr(n, l1, sg1, 1);
+        for (int jj = 0; jj < R; ++jj) {
+            const double gj1 = fnode(ch, n, l1, sg1, 0, jj / R1), gj2 = fnode(ch, n, l1, sg1, 1, jj % R1);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < R; ++t) {
+                const double gb1 = fnode(ch, n, L - s, beta, 0, t / R1), gb2 = fnode(ch, n, L - s, beta, 1, t % R1);
+                const double2 w = zmul2(expi_d(phi2(kind, y1, y2, gb1, gb2) - phi2(kind, y1, y2, gj1, gj2)), c[t]);
+                const double q = lag1_d(ch, R1, jj / R1, (gb1 - f1) / fhalf(l1)) * lag1_d(ch, R1, jj % R1, (gb2 - f2) / fhalf(l1));
+                acc.x += q * w.x;
+                acc.y += q * w.y;
+            }
+            d[jj] = acc;
+        }
+        for (int t = 0; t < R; ++t) c[t] = d[t];
+    }
+    {   // M at level h
+        const int64_t tau = box_at(i1, i2, L, h), sg = box_at(j1, j2, L, L - h);
+        for (int ii = 0; ii < R; ++ii) {
+            const double z1 = snode(ch, h, tau, 0, ii / R1), z2 = snode(ch, h, tau, 1, ii % R1);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < R; ++t) {
+                const double g1 = fnode(ch, n, L - h, sg, 0, t / R1), g2 = fnode(ch, n, L - h, sg, 1, t % R1);
+                const double2 w = zmul2(zmul2(amp(z1, z2, g1, g2), expi_d(phi2(kind, z1, z2, g1, g2))), c[t]);
+                acc.x += w.x;
+                acc.y += w.y;
+            }
+            d[ii] = acc;
+        }
+    }
+    for (int s = h; s < sU; ++s) {   // B, pair level s -> s+1
+        const int64_t al = box_at(i1, i2, L, s), tau1 = box_at(i1, i2, L, s + 1), beta = box_at(j1, j2, L, L - s);
+        const double e1 = fctr(n, L - s, beta, 0), e2 = fctr(n, L - s, beta, 1);
+        const double ya1 = sctr(s, al, 0), ya2 = sctr(s, al, 1);
+        for (int ii = 0; ii < R; ++ii) {
+            const double z1 = snode(ch, s + 1, tau1, 0, ii / R1), z2 = snode(ch, s + 1, tau1, 1, ii % R1);
+            const double p1 = ldexp(1.0, s + 1) * (z1 - ya1), p2 = ldexp(1.0, s + 1) * (z2 - ya2);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < R; ++t) {
+                const double za1 = snode(ch, s, al, 0, t / R1), za2 = snode(ch, s, al, 1, t % R1);
+                const double2 w = zmul2(expi_d(phi2(kind, z1, z2, e1, e2) - phi2(kind, za1, za2, e1, e2)), d[t]);
+                const double p = lag1_d(ch, R1, t / R1, p1) * lag1_d(ch, R1, t % R1, p2);
+                acc.x += p * w.x;
+                acc.y += p * w.y;
+            }
+            c[ii] = acc;
+        }
+        for (int t = 0; t < R; ++t) d[t] = c[t];
+    }
+    double2 y = make_double2(0.0, 0.0);
+    {   // U at space level sU
+        const int64_t tau = box_at(i1, i2, L, sU), sg = box_at(j1, j2, L, L - sU);
+        const double e1 = fctr(n, L - sU, sg, 0), e2 = fctr(n, L - sU, sg, 1);
+        const double p1 = ldexp(1.0, sU + 1) * (x1 - sctr(sU, tau, 0)), p2 = ldexp(1.0, sU + 1) * (x2 - sctr(sU, tau, 1));
+        for (int t = 0; t < R; ++t) {
+            const double z1 = snode(ch, sU, tau, 0, t / R1), z2 = snode(ch, sU, tau, 1, t % R1);
+            const double2 w = zmul2(expi_d(phi2(kind, x1, x2, e1, e2) - phi2(kind, z1, z2, e1, e2)), d[t]);
+            const double p = lag1_d(ch, R1, t / R1, p1) * lag1_d(ch, R1, t % R1, p2);
+            y.x += p * w.x;
+            y.y += p * w.y;
+        }
+    }
+    out[2 * e] = y;
+    out[2 * e + 1] = zmul2(amp(x1, x2, k1, k2), expi_d(phi2(kind, x1, x2, k1, k2)));
+}
+
 // Lexicographic <- Morton reordering of frequency vectors: X[j] = Xm[morton(j)].
 __global__ void k2_unmorton(const float2* __restrict__ Xm, float2* __restrict__ X, int n, int L, int64_t ld) {
     const int64_t N = int64_t(n) * n;
@@ -473,14 +634,20 @@ __global__ void k2_unmorton(const float2* __restrict__ Xm, float2* __restrict__ 
     X[col * ld + j] = Xm[col * ld + morton(int(j / n), int(j % n), L)];
 }
 
-constexpr size_t kSmemVadj = (64 * 65 + 4 * 64 * R) * sizeof(float2) + R * 64 * sizeof(float);
-constexpr size_t kSmemUfwd = (64 * 65 + 4 * 64 * R) * sizeof(float2) + 64 * R * sizeof(float);
-constexpr size_t kSmemM = 16 * R * R * sizeof(float2);
+template <int R1>
+constexpr size_t smem_leaf() {   // V^* and U: 64 x 65 phases, 4 columns x 64 x R states, 64 x R basis values
+    return (64 * 65 + 4 * 64 * G2<R1>::R) * sizeof(float2) + G2<R1>::R * 64 * sizeof(float);
+}
+template <int R1>
+constexpr size_t smem_mid() {
+    return size_t(G2<R1>::MP) * G2<R1>::R * G2<R1>::R * sizeof(float2);
+}
 
+// real tables: Pc | Pc^T (4 children x R rows of RP) | QV (R x NA) | QU (NP x R)
 size_t off_P() { return 0; }
-size_t off_PT() { return size_t(4) * R * RP; }
-size_t off_QV() { return size_t(8) * R * RP; }
-size_t off_QU(int NA) { return off_QV() + size_t(R) * NA; }
+size_t off_PT(int R, int RP) { return size_t(4) * R * RP; }
+size_t off_QV(int R, int RP) { return size_t(8) * R * RP; }
+size_t off_QU(int R, int RP, int NA) { return off_QV(R, RP) + size_t(R) * NA; }
 
 }  // namespace
 
@@ -488,30 +655,36 @@ bool bf2d_ok_kind(int kind) {
     return kind == FIO_PHASE_DFT || kind == FIO_PHASE_2D_ELLIPTIC || kind == FIO_PHASE_2D_ISO;
 }
 
-fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
-    const int n = bf->nside, L = bf->L, r1 = R1;
+bool bf2d_ok_r1(int r1) { return r1 >= kMinR1 && r1 <= kMaxR1; }
+
+namespace {
+
+template <int R1>
+fio_status build2(fio_bf* bf, cudaStream_t st) {
+    constexpr int R = G2<R1>::R, RP = G2<R1>::RP;
+    const int n = bf->nside, L = bf->L;
     const int NA = 1 << (2 * bf->sV), NP = 1 << (2 * (L - bf->sU));
     const int mV = 1 << bf->sV, mU = 1 << (L - bf->sU);
-    Cheb5 ch;
-    for (int k = 0; k < r1; ++k) ch.t[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * r1));
+    Cheb2 ch{};
+    for (int k = 0; k < R1; ++k) ch.t[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * R1));
     // real tables: Pc, Pc^T, QV, QU
-    std::vector<float> P(off_QU(NA) + size_t(NP) * R, 0.f);
-    auto l1 = [&](int k, double u) { return lagrange_host(ch.t, r1, k, u); };
+    std::vector<float> P(off_QU(R, RP, NA) + size_t(NP) * R, 0.f);
+    auto l1 = [&](int k, double u) { return lagrange_host(ch.t, R1, k, u); };
     for (int c = 0; c < 4; ++c)
         for (int j = 0; j < R; ++j)
             for (int t = 0; t < R; ++t) {
-                const double v = l1(j / r1, (c >> 1) - 0.5 + 0.5 * ch.t[t / r1]) * l1(j % r1, (c & 1) - 0.5 + 0.5 * ch.t[t % r1]);
+                const double v = l1(j / R1, (c >> 1) - 0.5 + 0.5 * ch.t[t / R1]) * l1(j % R1, (c & 1) - 0.5 + 0.5 * ch.t[t % R1]);
                 P[off_P() + (c * R + j) * RP + t] = float(v);
-                P[off_PT() + (c * R + t) * RP + j] = float(v);
+                P[off_PT(R, RP) + (c * R + t) * RP + j] = float(v);
             }
     for (int t = 0; t < R; ++t)
         for (int q = 0; q < NA; ++q)
-            P[off_QV() + t * NA + q] =
-                float(l1(t / r1, 2.0 * (q / mV) / mV - 1.0) * l1(t % r1, 2.0 * (q % mV) / mV - 1.0));
+            P[off_QV(R, RP) + t * NA + q] =
+                float(l1(t / R1, 2.0 * (q / mV) / mV - 1.0) * l1(t % R1, 2.0 * (q % mV) / mV - 1.0));
     for (int x = 0; x < NP; ++x)
         for (int i = 0; i < R; ++i)
-            P[off_QU(NA) + x * R + i] =
-                float(l1(i / r1, 2.0 * (x / mU) / mU - 1.0) * l1(i % r1, 2.0 * (x % mU) / mU - 1.0));
+            P[off_QU(R, RP, NA) + x * R + i] =
+                float(l1(i / R1, 2.0 * (x / mU) / mU - 1.0) * l1(i % R1, 2.0 * (x % mU) / mU - 1.0));
     FIO_TRY(bf->P.ensure(P.size() * sizeof(float)));
     FIO_CUDA(cudaMemcpyAsync(bf->P.p, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     const int64_t N = int64_t(n) * n;
@@ -522,84 +695,146 @@ fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
     FIO_TRY(bf->M.ensure(nM * 8));
     k2_tab_VP<<<cdiv(nVP, TB), TB, 0, st>>>(bf->VP.as<float2>(), kind, n, bf->sV);
     k2_tab_UP<<<cdiv(nUP, TB), TB, 0, st>>>(bf->UP.as<float2>(), kind, n, L, bf->sU);
-    k2_tab_M<<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), kind, bf->amp.kind, ch, n, L, bf->h);
+    k2_tab_M<R1><<<cdiv(nM, TB), TB, 0, st>>>(bf->M.as<float2>(), kind, bf->amp.kind, ch, n, L, bf->h);
     bf->C.resize(bf->h - bf->sV);
     for (int s = bf->sV; s < bf->h; ++s) {
         FIO_TRY(bf->C[s - bf->sV].ensure(nT * 8));
-        k2_tab_F<<<cdiv(nT, TB), TB, 0, st>>>(bf->C[s - bf->sV].as<float2>(), kind, ch, n, L, s);
+        k2_tab_F<R1><<<cdiv(nT, TB), TB, 0, st>>>(bf->C[s - bf->sV].as<float2>(), kind, ch, n, L, s);
     }
     bf->B.resize(bf->sU - bf->h);
     for (int s = bf->h; s < bf->sU; ++s) {
         FIO_TRY(bf->B[s - bf->h].ensure(nT * 8));
-        k2_tab_E<<<cdiv(nT, TB), TB, 0, st>>>(bf->B[s - bf->h].as<float2>(), kind, ch, n, L, s);
+        k2_tab_E<R1><<<cdiv(nT, TB), TB, 0, st>>>(bf->B[s - bf->h].as<float2>(), kind, ch, n, L, s);
     }
     FIO_CUDA(cudaGetLastError());
     FIO_CUDA(cudaStreamSynchronize(st));
     bf->table_bytes = (nVP + nUP + nM + nT * int64_t(bf->C.size() + bf->B.size())) * 8 + int64_t(P.size()) * 4;
     static PerDeviceOnce attrs;
     FIO_CUDA(attrs.run([] {
-        cudaError_t e = cudaFuncSetAttribute(k2_V_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemVadj));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k2_U_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemUfwd));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k2_M<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k2_M<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemM));
+        constexpr int sl = int(smem_leaf<R1>()), sm = int(smem_mid<R1>());
+        cudaError_t e = cudaFuncSetAttribute(k2_V_adj<R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_U_fwd<R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_M<R1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_M<R1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         return e;
     }));
     return FIO_OK;
 }
 
-// kc columns; states s0, s1 of N * 25 * kc complex each.
-fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool mort,
-                           float2* s0, float2* s1, cudaStream_t st) {
+// kc columns; states s0, s1 of N * R * kc complex each.
+template <int R1>
+fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool mort, float2* s0,
+                  float2* s1, cudaStream_t st) {
+    constexpr int R = G2<R1>::R, RP = G2<R1>::RP, MP = G2<R1>::MP;
+    constexpr size_t sl = smem_leaf<R1>(), sm = smem_mid<R1>();
     const int n = bf->nside, L = bf->L, h = bf->h, sU = bf->sU, sV = bf->sV;
     const int64_t N = int64_t(n) * n, SN = N * R;
     const int NA = 1 << (2 * sV);
     const float* Pm = bf->P.as<float>();
-    const float* QV = Pm + off_QV();
-    const float* QU = Pm + off_QU(NA);
+    const float* QV = Pm + off_QV(R, RP);
+    const float* QU = Pm + off_QU(R, RP, NA);
+    const float* Pc = Pm + off_P();
+    const float* PcT = Pm + off_PT(R, RP);
     const int64_t ngroups = N / 4;
     const unsigned gtr = cdiv(ngroups * kc, TB / 4);
     const dim3 gV(unsigned(int64_t(1) << (2 * (L - sV))), cdiv(kc, 4));
     const dim3 gU(unsigned(int64_t(1) << (2 * sU)), cdiv(kc, 4));
-    const dim3 gM(cdiv(N, 16), cdiv(kc, 16));
+    const dim3 gM(cdiv(N, MP), cdiv(kc, TB / MP));
     float2* cur = s0;
     float2* oth = s1;
     const int m = mort ? 1 : 0;
     if (!adjoint) {
-        FIO_LAUNCH("k2_V_fwd", st, k2_V_fwd<<<gV, TB, 0, st>>>(X, ld, cur, SN, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
+        FIO_LAUNCH("k2_V_fwd", st, k2_V_fwd<R1><<<gV, TB, 0, st>>>(X, ld, cur, SN, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
         for (int s = sV; s < h; ++s) {
-            FIO_LAUNCH("k2_C_fwd", st, (k2_trans<true, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
-                                                                                 Pm + off_P(), L, s, kc)));
+            FIO_LAUNCH("k2_C_fwd", st, (k2_trans<R1, true, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+                                                                                     Pc, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_M_fwd", st, k2_M<false><<<gM, TB, kSmemM, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc));
+        FIO_LAUNCH("k2_M_fwd", st, (k2_M<R1, false><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h; s < sU; ++s) {
-            FIO_LAUNCH("k2_B_fwd", st, (k2_trans<false, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
-                                                                                  Pm + off_PT(), L, s, kc)));
+            FIO_LAUNCH("k2_B_fwd", st, (k2_trans<R1, false, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+                                                                                      PcT, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_U_fwd", st, k2_U_fwd<<<gU, TB, kSmemUfwd, st>>>(cur, SN, Y, ld, bf->UP.as<float2>(), QU, n, L, sU, kc));
+        FIO_LAUNCH("k2_U_fwd", st, k2_U_fwd<R1><<<gU, TB, sl, st>>>(cur, SN, Y, ld, bf->UP.as<float2>(), QU, n, L, sU, kc));
     } else {
-        FIO_LAUNCH("k2_U_adj", st, k2_U_adj<<<gU, TB, 0, st>>>(X, ld, cur, SN, bf->UP.as<float2>(), QU, n, L, sU, kc));
+        FIO_LAUNCH("k2_U_adj", st, k2_U_adj<R1><<<gU, TB, 0, st>>>(X, ld, cur, SN, bf->UP.as<float2>(), QU, n, L, sU, kc));
         for (int s = sU - 1; s >= h; --s) {
-            FIO_LAUNCH("k2_B_adj", st, (k2_trans<true, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
-                                                                                Pm + off_P(), L, s, kc)));
+            FIO_LAUNCH("k2_B_adj", st, (k2_trans<R1, true, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+                                                                                    Pc, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_M_adj", st, k2_M<true><<<gM, TB, kSmemM, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc));
+        FIO_LAUNCH("k2_M_adj", st, (k2_M<R1, true><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h - 1; s >= sV; --s) {
-            FIO_LAUNCH("k2_C_adj", st, (k2_trans<false, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
-                                                                                 Pm + off_PT(), L, s, kc)));
+            FIO_LAUNCH("k2_C_adj", st, (k2_trans<R1, false, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+                                                                                     PcT, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_V_adj", st, k2_V_adj<<<gV, TB, kSmemVadj, st>>>(cur, SN, Y, ld, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
+        FIO_LAUNCH("k2_V_adj", st, k2_V_adj<R1><<<gV, TB, sl, st>>>(cur, SN, Y, ld, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
+}
+
+int r1_of(const fio_bf* bf) {
+    int r1 = 1;
+    while ((r1 + 1) * (r1 + 1) <= bf->r) ++r1;
+    return r1;
+}
+
+}  // namespace
+
+fio_status bf2d_build(fio_bf* bf, cudaStream_t st) {
+    switch (r1_of(bf)) {
+        case 3: return build2<3>(bf, st);
+        case 4: return build2<4>(bf, st);
+        case 5: return build2<5>(bf, st);
+        case 6: return build2<6>(bf, st);
+        case 7: return build2<7>(bf, st);
+    }
+    return fail(FIO_EINVAL, "bf_build: 2D needs r = r1^2 with 3 <= r1 <= 7");
+}
+
+fio_status bf2d_apply_cols(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int kc, int adjoint, bool mort,
+                           float2* s0, float2* s1, cudaStream_t st) {
+    switch (r1_of(bf)) {
+        case 3: return apply2<3>(bf, X, Y, ld, kc, adjoint, mort, s0, s1, st);
+        case 4: return apply2<4>(bf, X, Y, ld, kc, adjoint, mort, s0, s1, st);
+        case 5: return apply2<5>(bf, X, Y, ld, kc, adjoint, mort, s0, s1, st);
+        case 6: return apply2<6>(bf, X, Y, ld, kc, adjoint, mort, s0, s1, st);
+        case 7: return apply2<7>(bf, X, Y, ld, kc, adjoint, mort, s0, s1, st);
+    }
+    return fail(FIO_EINVAL, "bf_apply: 2D handle with an unsupported rank");
+}
+
+namespace {
+template <int R1>
+fio_status entries2(const fio_phase& phase, int amp_kind, int n, const int64_t* rows, const int64_t* cols, int S,
+                    double2* out, cudaStream_t st) {
+    const int L = ilog2_exact(n);
+    const int h = L / 2, sU = std::max(L - 3, h), sV = std::min(3, h);
+    Cheb2 ch{};
+    for (int k = 0; k < R1; ++k) ch.t[k] = std::cos((2.0 * k + 1.0) * M_PI / (2.0 * R1));
+    const Ph2 kind{phase.kind, phase.s};
+    FIO_LAUNCH("k2_entry_chain", st,
+               (k2_entry_chain<R1><<<cdiv(S, 64), 64, 0, st>>>(rows, cols, S, kind, amp_kind, ch, n, L, h, sU, sV, out)));
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+}  // namespace
+
+fio_status bf2d_entries(const fio_phase& phase, int amp_kind, int n, int r1, const int64_t* rows, const int64_t* cols,
+                        int S, double2* out, cudaStream_t st) {
+    switch (r1) {
+        case 3: return entries2<3>(phase, amp_kind, n, rows, cols, S, out, st);
+        case 4: return entries2<4>(phase, amp_kind, n, rows, cols, S, out, st);
+        case 5: return entries2<5>(phase, amp_kind, n, rows, cols, S, out, st);
+        case 6: return entries2<6>(phase, amp_kind, n, rows, cols, S, out, st);
+        case 7: return entries2<7>(phase, amp_kind, n, rows, cols, S, out, st);
+    }
+    return fail(FIO_EINVAL, "2D rank r1 must be in [3, 7]");
 }
 
 fio_status bf2d_unmorton(const fio_bf* bf, const float2* Xm, float2* X, int64_t ld, int k, cudaStream_t st) {

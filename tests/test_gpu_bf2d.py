@@ -1,4 +1,4 @@
-"""2D butterfly (quadtree, r = 25) and the 2D online solve against the oracle.
+"""2D butterfly (quadtree, r = r1^2; the workloads use r1 = 5) and the 2D online solve against the oracle.
 
 Tolerances: FP32 bf_apply rel-l2 <= 1e-5 against the oracle's apply of the
 same factors; GPU solve error against f_true no worse than 2x the oracle's.
@@ -34,6 +34,19 @@ def test_bf2d_apply_matches_oracle(n, k):
     ob = Butterfly2D(Phase("elliptic2d"), n, 5)
     gb = BF(n, 25, "elliptic2d")
     f = crandn(n * n, k, seed=100 * n + k)
+    assert rel(to_np(gb.apply(to_dev(f))), ob.apply(f)) < TOL
+    assert rel(to_np(gb.adjoint(to_dev(f))), ob.adjoint(f)) < TOL
+
+
+@pytest.mark.parametrize("r1", [3, 4, 6, 7])
+@pytest.mark.parametrize("n,k", [(32, 5), (128, 3), (256, 1)])
+def test_bf2d_apply_other_grids_match_oracle(r1, n, k):
+    """Grids r1 x r1 other than the workloads' 5 x 5: n = 32 (leaves only), 128 (one B level),
+    256 (one C and one B level); k = 5 is ragged over the 4-column leaf CTAs."""
+    from paper_2609_11520_b300 import BF
+    ob = Butterfly2D(Phase("elliptic2d"), n, r1)
+    gb = BF(n, r1 * r1, "elliptic2d")
+    f = crandn(n * n, k, seed=7 * n + r1)
     assert rel(to_np(gb.apply(to_dev(f))), ob.apply(f)) < TOL
     assert rel(to_np(gb.adjoint(to_dev(f))), ob.adjoint(f)) < TOL
 
@@ -78,7 +91,11 @@ def test_bf2d_adjoint_identity_full_size():
 def test_bf2d_rejections():
     from paper_2609_11520_b300 import BF, Batch, FioError, HSS
     with pytest.raises(FioError):
-        BF(64, 16, "elliptic2d")                     # 2D needs r = 25
+        BF(64, 20, "elliptic2d")                     # 2D needs r = r1^2
+    with pytest.raises(FioError):
+        BF(64, 64, "elliptic2d")                     # r1 <= 7
+    with pytest.raises(FioError):
+        BF(64, 4, "elliptic2d")                      # r1 >= 3
     with pytest.raises(FioError):
         BF(4, 25, "elliptic2d")                      # n >= 8
     with pytest.raises(FioError):
