@@ -282,6 +282,234 @@ __global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict_
                          blockIdx.z * RB);
 }
 
+// Wide node products (many columns): one CTA per (node, 64 columns, 128 rows), 256 threads as
+// 16 x 16, each owning 8 rows x 4 columns (rows ty + 16 a, columns tx + 16 b); W and x staged
+// through shared memory in tiles of 16 inner indices, so each W block is read once per
+// 64 columns.  Same operands and outputs as k_ulv_node_gemm.
+constexpr int kWideRows = 128, kWideCols = 64, kWideJ = 16;
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_ulv_wide(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
+                                                  int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
+                                                  float2* __restrict__ outC, int nC, int64_t ldC,
+                                                  float2* __restrict__ outD, int64_t ldD, int k) {
+    __shared__ float2 sw[kWideJ][kWideRows + 1];
+    __shared__ float2 sx[kWideJ][kWideCols + 1];
+    const int t = blockIdx.x, c0 = blockIdx.y * kWideCols, r0 = blockIdx.z * kWideRows;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int kc = min(kWideCols, k - c0), nr = min(kWideRows, m - r0);
+    const float2* Wt = W + int64_t(t) * m * m;
+    float2 acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < m; j0 += kWideJ) {
+        const int jw = min(kWideJ, m - j0);
+        for (int e = tid; e < kWideJ * kWideRows; e += 256) {
+            int jj, il;
+            if (!CONJ) {   // column j of W, rows r0..: consecutive il
+                il = e % kWideRows;
+                jj = e / kWideRows;
+            } else {       // row j of W^*: W[j + i m], consecutive jj
+                jj = e % kWideJ;
+                il = e / kWideJ;
+            }
+            float2 v = make_float2(0.f, 0.f);
+            if (jj < jw && il < nr)
+                v = CONJ ? Wt[(j0 + jj) + int64_t(r0 + il) * m] : Wt[(r0 + il) + int64_t(j0 + jj) * m];
+            sw[jj][il] = v;
+        }
+        for (int e = tid; e < kWideJ * kWideCols; e += 256) {
+            const int jj = e % kWideJ, c = e / kWideJ, j = j0 + jj;
+            float2 v = make_float2(0.f, 0.f);
+            if (jj < jw && c < kc)
+                v = (j < nA) ? inA[int64_t(c0 + c) * ldA + int64_t(t) * nA + j]
+                             : inB[int64_t(c0 + c) * ldB + int64_t(t) * (m - nA) + (j - nA)];
+            sx[jj][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < kWideJ; ++jj) {
+            float2 av[8], bv[4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) av[a] = sw[jj][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = sx[jj][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if (CONJ) cfmac(acc[a][b], av[a], bv[b]);
+                    else cfma(acc[a][b], av[a], bv[b]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int il = ty + 16 * a;
+        if (il >= nr) continue;
+        const int i = r0 + il;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = tx + 16 * b;
+            if (c >= kc) continue;
+            if (i < nC) outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = acc[a][b];
+            else outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[a][b];
+        }
+    }
+}
+
+// Skinny node products (k <= KC <= 8 columns): one CTA of 128 threads per (node, 128 rows), one
+// output row per thread; W streamed from HBM once with eight loads in flight per thread (up pass:
+// coalesced column segments; down pass: each thread's own contiguous column of W, i.e. a row of
+// W^*); x staged through shared memory in tiles of 512 inner indices.
+constexpr int kSkinnyJ = 512;
+template <bool CONJ, int KC>
+__global__ void __launch_bounds__(128) k_ulv_skinny(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
+                                                    int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
+                                                    float2* __restrict__ outC, int nC, int64_t ldC,
+                                                    float2* __restrict__ outD, int64_t ldD, int k) {
+    __shared__ float2 sx[kSkinnyJ][KC];
+    const int t = blockIdx.x, il = threadIdx.x, i = blockIdx.y * 128 + il;
+    const float2* Wt = W + int64_t(t) * m * m;
+    float2 acc[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < m; j0 += kSkinnyJ) {
+        const int jw = min(kSkinnyJ, m - j0);
+        __syncthreads();
+        for (int e = il; e < kSkinnyJ * KC; e += 128) {
+            const int jj = e % kSkinnyJ, c = e / kSkinnyJ, j = j0 + jj;
+            float2 v = make_float2(0.f, 0.f);
+            if (jj < jw && c < k)
+                v = (j < nA) ? inA[int64_t(c) * ldA + int64_t(t) * nA + j]
+                             : inB[int64_t(c) * ldB + int64_t(t) * (m - nA) + (j - nA)];
+            sx[jj][c] = v;
+        }
+        __syncthreads();
+        if (i < m) {
+            if (!CONJ) {
+                const float2* wp = Wt + i + int64_t(j0) * m;
+#pragma unroll 8
+                for (int jj = 0; jj < jw; ++jj) {
+                    const float2 w = __ldg(wp + int64_t(jj) * m);
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) cfma(acc[c], w, sx[jj][c]);
+                }
+            } else {
+                const float2* wp = Wt + int64_t(i) * m + j0;
+#pragma unroll 8
+                for (int jj = 0; jj < jw; ++jj) {
+                    const float2 w = __ldg(wp + jj);
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) cfmac(acc[c], w, sx[jj][c]);
+                }
+            }
+        }
+    }
+    if (i >= m) return;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+        if (c >= k) break;
+        if (i < nC) outC[int64_t(c) * ldC + int64_t(t) * nC + i] = acc[c];
+        else outD[int64_t(c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[c];
+    }
+}
+
+// The small upper levels of a solve with few columns in one CTA: up pass of levels lu..1, the root
+// product c_0 = Rinv y_0 and the down pass of levels 1..lu, one output element per thread and
+// step (dot products straight from the W blocks), a barrier between levels.
+constexpr int kUpperMaxLevels = 32;
+struct UpperArgs {
+    const float2* W[kUpperMaxLevels];
+    int m[kUpperMaxLevels], r[kUpperMaxLevels];
+    int64_t ob[kUpperMaxLevels], oy[kUpperMaxLevels], oc[kUpperMaxLevels], rows[kUpperMaxLevels];
+    const float2* Rinv;
+    int m0, lu, k;
+    float2* w;   // solve workspace; vectors at offsets (ob, oy, oc) x k
+};
+__global__ void __launch_bounds__(1024) k_ulv_upper(const UpperArgs a) {
+    const int tid = threadIdx.x, nt = blockDim.x, k = a.k;
+    auto bh = [&](int l) { return a.w + a.ob[l] * k; };
+    auto yv = [&](int l) { return a.w + a.oy[l] * k; };
+    auto cv = [&](int l) { return a.w + a.oc[l] * k; };
+    for (int l = a.lu; l >= 1; --l) {   // z = W_t y_t: rows [0, m - r) to b^_1, [m - r, m) to y_{l-1}
+        const int m = a.m[l], r = a.r[l], nn = 1 << l;
+        if (m > 0) {
+            const float2* in = yv(l);
+            const int64_t ldin = a.rows[l], nb = max(int64_t(nn) * (m - r), int64_t(1));
+            const int64_t ldy = max(a.rows[l - 1], int64_t(1));
+            const float2* Wl = a.W[l];
+            for (int e = tid; e < nn * m * k; e += nt) {
+                const int i = e % m, rest = e / m, t = rest % nn, c = rest / nn;
+                const float2* Wt = Wl + int64_t(t) * m * m;
+                const float2* x = in + int64_t(c) * ldin + int64_t(t) * m;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int j = 0; j < m; ++j) cfma(acc, Wt[i + int64_t(j) * m], x[j]);
+                if (i < m - r) bh(l)[int64_t(c) * nb + int64_t(t) * (m - r) + i] = acc;
+                else yv(l - 1)[int64_t(c) * ldy + int64_t(t) * r + (i - (m - r))] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < a.m0 * k; e += nt) {
+        const int i = e % a.m0, c = e / a.m0;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int j = 0; j < a.m0; ++j) cfma(acc, a.Rinv[i + int64_t(j) * a.m0], yv(0)[int64_t(c) * a.m0 + j]);
+        cv(0)[int64_t(c) * a.m0 + i] = acc;
+    }
+    __syncthreads();
+    for (int l = 1; l <= a.lu; ++l) {   // c_t = W_t^* [b^_1; c_2] -> c_l
+        const int m = a.m[l], r = a.r[l], nn = 1 << l;
+        if (m > 0) {
+            const int64_t nb = max(int64_t(nn) * (m - r), int64_t(1)), ldp = max(a.rows[l - 1], int64_t(1));
+            const int64_t ldo = a.rows[l];
+            const float2* Wl = a.W[l];
+            for (int e = tid; e < nn * m * k; e += nt) {
+                const int i = e % m, rest = e / m, t = rest % nn, c = rest / nn;
+                const float2* Wt = Wl + int64_t(t) * m * m + int64_t(i) * m;
+                const float2* x1 = bh(l) + int64_t(c) * nb + int64_t(t) * (m - r);
+                const float2* x2 = cv(l - 1) + int64_t(c) * ldp + int64_t(t) * r;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int j = 0; j < m - r; ++j) cfmac(acc, Wt[j], x1[j]);
+                for (int j = m - r; j < m; ++j) cfmac(acc, Wt[j], x2[j - (m - r)]);
+                cv(l)[int64_t(c) * ldo + int64_t(t) * m + i] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kSkinnyMaxK = 8;
+
+// The node products of one solve level with the kernel that suits k: skinny (k <= 8), wide
+// (m >= 32), else the tiled k_ulv_node_gemm.
+template <bool CONJ>
+fio_status node_products(const char* name, const float2* W, int m, const float2* inA, int nA, int64_t ldA,
+                         const float2* inB, int64_t ldB, float2* outC, int nC, int64_t ldC, float2* outD, int64_t ldD,
+                         int k, int nodes, cudaStream_t st) {
+    if (k <= kSkinnyMaxK) {
+        const dim3 g(nodes, cdiv(m, 128));
+        if (k == 1)
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 1><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+        else if (k == 2)
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 2><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+        else if (k <= 4)
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 4><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+        else
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 8><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+    } else if (m >= 32) {
+        const dim3 g(nodes, cdiv(k, kWideCols), cdiv(m, kWideRows));
+        FIO_LAUNCH(name, st, (k_ulv_wide<CONJ><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+    } else {
+        const dim3 g(nodes, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
+        FIO_LAUNCH(name, st, (k_ulv_node_gemm<CONJ><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+    }
+    FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
 // Grouped node products: CTA b runs item (descriptor, node, first column, first row).
 template <bool CONJ>
 __global__ void __launch_bounds__(256) k_ulv_node_gemm_group(const UlvGemmDesc* __restrict__ d,
@@ -479,35 +707,60 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
     auto cv = [&](int l) { return w + oc[l] * k; };
     const float2* B = static_cast<const float2*>(Bv);
     float2* X = static_cast<float2*>(Xv);
-    for (int l = Lh; l >= 1; --l) {
+    // few columns: the small upper levels (m_l <= 64) and the root run in one single-CTA launch
+    const int m0 = 2 * h->ranks[1];
+    int lu = 0;
+    if (k <= kSkinnyMaxK && m0 <= 128 && Lh - 1 < kUpperMaxLevels) {
+        int64_t work = int64_t(m0) * m0 * k;
+        for (int l = 1; l < Lh; ++l) {
+            const int m = h->m(l);
+            work += (int64_t(1) << l) * m * m * k;
+            if (m > 64 || work > (int64_t(1) << 21)) break;
+            lu = l;
+        }
+    }
+    for (int l = Lh; l > lu; --l) {
         const int m = h->m(l), r = h->ranks[l];
         if (m == 0) continue;   // every rank above this level is 0: nothing to pass up
         const float2* in = (l == Lh) ? B : yv(l);
         int64_t ldin = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        dim3 gg(1 << l, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
-        FIO_LAUNCH("k_ulv_up", st,
-                   k_ulv_node_gemm<false><<<gg, 256, 0, st>>>(h->W[l].as<float2>(), m, in, m, ldin, in, ldin, bh(l),
-                                                                m - r, std::max<int64_t>(nb, 1), yv(l - 1),
-                                                                std::max<int64_t>(h->rows(l - 1), 1), k));
+        FIO_TRY(node_products<false>("k_ulv_up", h->W[l].as<float2>(), m, in, m, ldin, in, ldin, bh(l), m - r,
+                                     std::max<int64_t>(nb, 1), yv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), k,
+                                     1 << l, st));
     }
-    const int m0 = 2 * h->ranks[1];
-    if (m0 > 0) {
+    if (lu > 0) {
+        UpperArgs ua{};
+        for (int l = 1; l <= lu; ++l) {
+            ua.W[l] = h->W[l].as<float2>();
+            ua.m[l] = h->m(l);
+            ua.r[l] = h->ranks[l];
+        }
+        for (int l = 0; l <= lu; ++l) {
+            ua.ob[l] = ob[l];
+            ua.oy[l] = oy[l];
+            ua.oc[l] = oc[l];
+            ua.rows[l] = h->rows(l);
+        }
+        ua.Rinv = h->Rinv.as<float2>();
+        ua.m0 = m0;
+        ua.lu = lu;
+        ua.k = k;
+        ua.w = w;
+        FIO_LAUNCH("k_ulv_upper", st, k_ulv_upper<<<1, 1024, 0, st>>>(ua));
+    } else if (m0 > 0) {
         dim3 g(cdiv(m0, TB), k);
         FIO_LAUNCH("k_ulv_root", st, k_gemv_sq<<<g, TB, 0, st>>>(h->Rinv.as<float2>(), m0, yv(0), m0, cv(0), m0));
     }
-    for (int l = 1; l <= Lh; ++l) {
+    for (int l = lu + 1; l <= Lh; ++l) {
         const int m = h->m(l), r = h->ranks[l];
         if (m == 0) continue;
         float2* out = (l == Lh) ? X : cv(l);
         int64_t ldo = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        dim3 gg(1 << l, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
-        FIO_LAUNCH("k_ulv_down", st,
-                   k_ulv_node_gemm<true><<<gg, 256, 0, st>>>(h->W[l].as<float2>(), m, bh(l), m - r,
-                                                               std::max<int64_t>(nb, 1), cv(l - 1),
-                                                               std::max<int64_t>(h->rows(l - 1), 1), out, m, ldo, out,
-                                                               ldo, k));
+        FIO_TRY(node_products<true>("k_ulv_down", h->W[l].as<float2>(), m, bh(l), m - r, std::max<int64_t>(nb, 1),
+                                    cv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), out, m, ldo, out, ldo, k, 1 << l,
+                                    st));
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;
