@@ -367,6 +367,17 @@ def run_2d(args):
     e = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
     fio_solve(bs, g, U, out=OUT, refine_steps=1)
     e1 = float(torch.linalg.norm(OUT - Ft) / torch.linalg.norm(Ft))
+    _lib.lib.fio_profile_enable(1)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        fio_solve(bs, g, U, out=OUT)
+    torch.cuda.synchronize()
+    _lib.check(_lib.lib.fio_profile_report(buf, len(buf)))
+    _lib.lib.fio_profile_enable(0)
+    sprof = parse_profile(buf.value.decode())
+    stot = sum(v[1] for v in sprof.values())
+    solve_kernels = {nm: {"launches": c, "ms_total": round(ms, 4), "share": round(ms / stot, 4)}
+                     for nm, (c, ms) in sorted(sprof.items(), key=lambda kv: -kv[1][1])}
     line = {
         "metric": f"2D K~^* apply RHS/s (n = 256, N = 2^16, quadtree BF r = {R}); 2D online solve", "unit": UNIT,
         "value": k * args.steps / (sum(adj) / 1e3), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -380,7 +391,8 @@ def run_2d(args):
                      "peak_source": peak_src, "bytes_per_launch": tb, "traffic": None},
         "solve": {"n": ns, "N": ns * ns, "r": R, "leaf": 256, "tol": 1e-3, "k": k, "hss_build_s": round(t_hss, 2),
                   "ulv_factor_s": round(t_fac, 2), "ranks": g.info()["ranks"], "rhs_per_s": k * args.steps / (sum(sol) / 1e3),
-                  "ms_per_solve": statistics.mean(sol), "e_direct_vs_f_true": e, "e_refine1": e1},
+                  "ms_per_solve": statistics.mean(sol), "e_direct_vs_f_true": e, "e_refine1": e1,
+                  "kernels": solve_kernels},
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

@@ -48,6 +48,11 @@ struct G2 {
     static constexpr int RP = (R + 3) / 4 * 4;
     static constexpr int PHG = R <= 25 ? 8 : (R <= 36 ? 2 : 1);
     static constexpr int MP = R <= 36 ? 16 : 8;
+    // r1 >= 6: the middle level splits each pair's R outputs into r1 chunks of r1 (one thread per
+    // chunk, MQ = MQP pairs x 16 columns x r1 threads per CTA), which keeps the registers low
+    static constexpr bool CHUNK_M = R1 >= 6;
+    static constexpr int MQP = 8;
+    static constexpr int MQ = MQP * 16 * R1;
 };
 
 // first-kind Chebyshev points on [-1, 1] of the handle's r1
@@ -413,6 +418,44 @@ __global__ void __launch_bounds__(TB) k2_M(const float2* __restrict__ Sin, float
     for (int v = 0; v < R; ++v) y[v] = acc[v];
 }
 
+// Middle level for r1 >= 6: CTA = MQP pairs x 16 columns x r1 chunks of r1 outputs; thread
+// (chunk, pair, column); the M blocks of the MQP pairs staged in shared memory.
+template <int R1, bool ADJ>
+__global__ void __launch_bounds__(G2<R1>::MQ) k2_Mq(const float2* __restrict__ Sin, float2* __restrict__ Sout,
+                                                    int64_t SN, const float2* __restrict__ M, int64_t npairs, int kc) {
+    constexpr int R = G2<R1>::R, MP = G2<R1>::MQP, MQ = G2<R1>::MQ;
+    extern __shared__ float4 smem_m[];
+    float2* Ms = reinterpret_cast<float2*>(smem_m);   // [MQP][R*R]
+    const int64_t p0 = int64_t(blockIdx.x) * MP;
+    const int np = int(std::min<int64_t>(MP, npairs - p0));
+    const float4* src = reinterpret_cast<const float4*>(M + p0 * R * R);
+    float4* dst = reinterpret_cast<float4*>(Ms);
+    for (int i = threadIdx.x; i < np * R * R / 2; i += MQ) dst[i] = src[i];   // p0 even: 16-byte aligned
+    if (np * R * R % 2 && threadIdx.x == 0) Ms[np * R * R - 1] = M[(p0 + np) * R * R - 1];
+    __syncthreads();
+    const int q = threadIdx.x % R1, rest = threadIdx.x / R1, pl = rest % MP;
+    const int col = blockIdx.y * 16 + rest / MP;
+    if (pl >= np || col >= kc) return;
+    const float2* m = Ms + pl * R * R;
+    const float2* x = Sin + col * SN + (p0 + pl) * R;
+    float2 acc[R1];
+#pragma unroll
+    for (int vv = 0; vv < R1; ++vv) acc[vv] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int w = 0; w < R; ++w) {
+        const float2 xw = __ldg(x + w);
+#pragma unroll
+        for (int vv = 0; vv < R1; ++vv) {
+            const int v = q * R1 + vv;
+            if (ADJ) cfmac(acc[vv], m[w * R + v], xw);
+            else cfma(acc[vv], m[v * R + w], xw);
+        }
+    }
+    float2* y = Sout + col * SN + (p0 + pl) * R + q * R1;
+#pragma unroll
+    for (int vv = 0; vv < R1; ++vv) y[vv] = acc[vv];
+}
+
 // U (forward): y(x) = sum_b UP[x][b] sum_i QU[x_loc][i] d(tau, b, i).
 // CTA: one space leaf tau, 4 columns; thread (x_loc, column).
 template <int R1>
@@ -640,7 +683,7 @@ constexpr size_t smem_leaf() {   // V^* and U: 64 x 65 phases, 4 columns x 64 x 
 }
 template <int R1>
 constexpr size_t smem_mid() {
-    return size_t(G2<R1>::MP) * G2<R1>::R * G2<R1>::R * sizeof(float2);
+    return size_t(G2<R1>::CHUNK_M ? G2<R1>::MQP : G2<R1>::MP) * G2<R1>::R * G2<R1>::R * sizeof(float2);
 }
 
 // real tables: Pc | Pc^T (4 children x R rows of RP) | QV (R x NA) | QU (NP x R)
@@ -716,6 +759,10 @@ fio_status build2(fio_bf* bf, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_U_fwd<R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_M<R1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_M<R1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess && G2<R1>::CHUNK_M)
+            e = cudaFuncSetAttribute(k2_Mq<R1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess && G2<R1>::CHUNK_M)
+            e = cudaFuncSetAttribute(k2_Mq<R1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         return e;
     }));
     return FIO_OK;
@@ -739,7 +786,7 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
     const unsigned gtr = cdiv(ngroups * kc, TB / 4);
     const dim3 gV(unsigned(int64_t(1) << (2 * (L - sV))), cdiv(kc, 4));
     const dim3 gU(unsigned(int64_t(1) << (2 * sU)), cdiv(kc, 4));
-    const dim3 gM(cdiv(N, MP), cdiv(kc, TB / MP));
+    const dim3 gM(cdiv(N, MP), cdiv(kc, TB / MP)), gMq(cdiv(N, G2<R1>::MQP), cdiv(kc, 16));
     float2* cur = s0;
     float2* oth = s1;
     const int m = mort ? 1 : 0;
@@ -750,7 +797,10 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
                                                                                      Pc, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_M_fwd", st, (k2_M<R1, false><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
+        if (G2<R1>::CHUNK_M)
+            FIO_LAUNCH("k2_M_fwd", st, (k2_Mq<R1, false><<<gMq, G2<R1>::MQ, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
+        else
+            FIO_LAUNCH("k2_M_fwd", st, (k2_M<R1, false><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h; s < sU; ++s) {
             FIO_LAUNCH("k2_B_fwd", st, (k2_trans<R1, false, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
@@ -765,7 +815,10 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
                                                                                     Pc, L, s, kc)));
             std::swap(cur, oth);
         }
-        FIO_LAUNCH("k2_M_adj", st, (k2_M<R1, true><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
+        if (G2<R1>::CHUNK_M)
+            FIO_LAUNCH("k2_M_adj", st, (k2_Mq<R1, true><<<gMq, G2<R1>::MQ, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
+        else
+            FIO_LAUNCH("k2_M_adj", st, (k2_M<R1, true><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h - 1; s >= sV; --s) {
             FIO_LAUNCH("k2_C_adj", st, (k2_trans<R1, false, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),

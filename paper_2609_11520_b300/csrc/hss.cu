@@ -867,6 +867,7 @@ extern "C" void hss_free(fio_hss* h) {
     h->D.release();
     h->Rinv.release();
     h->solve_ws.release();
+    h->solve_part.release();
     h->mv_ws.release();
     h->fio_ws.release();
     delete h;

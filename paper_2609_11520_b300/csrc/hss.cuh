@@ -16,6 +16,7 @@ struct fio_hss {
     std::vector<fio::DevBuf> W;
     fio::DevBuf Rinv;                // m_0 x m_0 (complex64)
     fio::DevBuf solve_ws;            // per-level vectors of the solve
+    fio::DevBuf solve_part;          // partial products of the sliced wide node products
     fio::DevBuf mv_ws;               // per-level vectors of the matvec
     fio::DevBuf fio_ws;              // K~^* u and refinement vectors of fio_solve
     int64_t samples = 0;

@@ -282,29 +282,37 @@ __global__ void __launch_bounds__(256) k_ulv_node_gemm(const float2* __restrict_
                          blockIdx.z * RB);
 }
 
-// Wide node products (many columns): one CTA per (node, 64 columns, 128 rows), 256 threads as
-// 16 x 16, each owning 8 rows x 4 columns (rows ty + 16 a, columns tx + 16 b); W and x staged
-// through shared memory in tiles of 16 inner indices, so each W block is read once per
-// 64 columns.  Same operands and outputs as k_ulv_node_gemm.
-constexpr int kWideRows = 128, kWideCols = 64, kWideJ = 16;
-template <bool CONJ>
+// Wide node products (k > 8): one CTA per (node, CB columns, 128 rows, slice of the inner index),
+// 256 threads as 16 x 16, each owning 8 rows x CB/16 columns (rows ty + 16 a, columns tx + 16 b);
+// W and x staged through shared memory in tiles of 16 inner indices, so each W block is read once
+// per CB columns.  With nsplit > 1 the inner index is cut into nsplit slices (levels with few
+// nodes and large m) whose partial products go to `part` ([slice][column][node][row]) and are
+// summed in slice order by k_ulv_wide_reduce; otherwise the CTA writes the outputs directly.
+// Same operands and outputs as k_ulv_node_gemm.
+constexpr int kWideRows = 128, kWideJ = 16;
+template <bool CONJ, int CB>
 __global__ void __launch_bounds__(256) k_ulv_wide(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
                                                   int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
                                                   float2* __restrict__ outC, int nC, int64_t ldC,
-                                                  float2* __restrict__ outD, int64_t ldD, int k) {
+                                                  float2* __restrict__ outD, int64_t ldD, int k, int nsplit, int jslice,
+                                                  float2* __restrict__ part) {
+    constexpr int NB = CB / 16;
     __shared__ float2 sw[kWideJ][kWideRows + 1];
-    __shared__ float2 sx[kWideJ][kWideCols + 1];
-    const int t = blockIdx.x, c0 = blockIdx.y * kWideCols, r0 = blockIdx.z * kWideRows;
+    __shared__ float2 sx[kWideJ][CB + 1];
+    const int t = blockIdx.x, nodes = gridDim.x;
+    const int cb = blockIdx.y / nsplit, sp = blockIdx.y % nsplit;
+    const int c0 = cb * CB, r0 = blockIdx.z * kWideRows;
+    const int jbeg = sp * jslice, jend = min(m, jbeg + jslice);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int kc = min(kWideCols, k - c0), nr = min(kWideRows, m - r0);
+    const int kc = min(CB, k - c0), nr = min(kWideRows, m - r0);
     const float2* Wt = W + int64_t(t) * m * m;
-    float2 acc[8][4];
+    float2 acc[8][NB];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
-    for (int j0 = 0; j0 < m; j0 += kWideJ) {
-        const int jw = min(kWideJ, m - j0);
+        for (int b = 0; b < NB; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int j0 = jbeg; j0 < jend; j0 += kWideJ) {
+        const int jw = min(kWideJ, jend - j0);
         for (int e = tid; e < kWideJ * kWideRows; e += 256) {
             int jj, il;
             if (!CONJ) {   // column j of W, rows r0..: consecutive il
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(256) k_ulv_wide(const float2* __restrict__ W, 
                 v = CONJ ? Wt[(j0 + jj) + int64_t(r0 + il) * m] : Wt[(r0 + il) + int64_t(j0 + jj) * m];
             sw[jj][il] = v;
         }
-        for (int e = tid; e < kWideJ * kWideCols; e += 256) {
+        for (int e = tid; e < kWideJ * CB; e += 256) {
             const int jj = e % kWideJ, c = e / kWideJ, j = j0 + jj;
             float2 v = make_float2(0.f, 0.f);
             if (jj < jw && c < kc)
@@ -330,15 +338,15 @@ __global__ void __launch_bounds__(256) k_ulv_wide(const float2* __restrict__ W, 
         __syncthreads();
 #pragma unroll
         for (int jj = 0; jj < kWideJ; ++jj) {
-            float2 av[8], bv[4];
+            float2 av[8], bv[NB];
 #pragma unroll
             for (int a = 0; a < 8; ++a) av[a] = sw[jj][ty + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = sx[jj][tx + 16 * b];
+            for (int b = 0; b < NB; ++b) bv[b] = sx[jj][tx + 16 * b];
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
+                for (int b = 0; b < NB; ++b) {
                     if (CONJ) cfmac(acc[a][b], av[a], bv[b]);
                     else cfma(acc[a][b], av[a], bv[b]);
                 }
@@ -351,13 +359,32 @@ __global__ void __launch_bounds__(256) k_ulv_wide(const float2* __restrict__ W, 
         if (il >= nr) continue;
         const int i = r0 + il;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < NB; ++b) {
             const int c = tx + 16 * b;
             if (c >= kc) continue;
-            if (i < nC) outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = acc[a][b];
-            else outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[a][b];
+            if (nsplit > 1)
+                part[((int64_t(sp) * k + c0 + c) * nodes + t) * m + i] = acc[a][b];
+            else if (i < nC)
+                outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = acc[a][b];
+            else
+                outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[a][b];
         }
     }
+}
+
+// Sum of the nsplit partial products in slice order, routed to outC / outD.
+__global__ void k_ulv_wide_reduce(const float2* __restrict__ part, int nsplit, int nodes, int m, int k,
+                                  float2* __restrict__ outC, int nC, int64_t ldC, float2* __restrict__ outD, int64_t ldD) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t per = int64_t(k) * nodes * m;
+    if (e >= per) return;
+    const int i = int(e % m);
+    const int64_t rest = e / m;
+    const int t = int(rest % nodes), c = int(rest / nodes);
+    float2 v = part[e];
+    for (int sp = 1; sp < nsplit; ++sp) v = cadd(v, part[sp * per + e]);
+    if (i < nC) outC[int64_t(c) * ldC + int64_t(t) * nC + i] = v;
+    else outD[int64_t(c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = v;
 }
 
 // Skinny node products (k <= KC <= 8 columns): one CTA of 128 threads per (node, 128 rows), one
@@ -483,12 +510,24 @@ __global__ void __launch_bounds__(1024) k_ulv_upper(const UpperArgs a) {
 
 constexpr int kSkinnyMaxK = 8;
 
+// Inner-index slices of a wide node product: enough CTAs for two waves on nsms SMs, slices of at
+// least 128 indices.
+int wide_cb(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
+int wide_nsplit(int m, int k, int nodes, int nsms) {
+    const int64_t ctas = int64_t(nodes) * cdiv(m, kWideRows) * cdiv(k, wide_cb(k));
+    if (ctas >= 2 * nsms) return 1;
+    const int ns = int(std::min<int64_t>(cdiv(2 * nsms, ctas), std::max(1, m / 128)));
+    const int jslice = kWideJ * cdiv(cdiv(m, ns), kWideJ);
+    return cdiv(m, jslice);
+}
+
 // The node products of one solve level with the kernel that suits k: skinny (k <= 8), wide
 // (m >= 32), else the tiled k_ulv_node_gemm.
+// part: scratch of at least wide_nsplit(m, k, nodes, nsms) * k * nodes * m complex.
 template <bool CONJ>
 fio_status node_products(const char* name, const float2* W, int m, const float2* inA, int nA, int64_t ldA,
                          const float2* inB, int64_t ldB, float2* outC, int nC, int64_t ldC, float2* outD, int64_t ldD,
-                         int k, int nodes, cudaStream_t st) {
+                         int k, int nodes, float2* part, int nsms, cudaStream_t st) {
     if (k <= kSkinnyMaxK) {
         const dim3 g(nodes, cdiv(m, 128));
         if (k == 1)
@@ -500,8 +539,22 @@ fio_status node_products(const char* name, const float2* W, int m, const float2*
         else
             FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 8><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
     } else if (m >= 32) {
-        const dim3 g(nodes, cdiv(k, kWideCols), cdiv(m, kWideRows));
-        FIO_LAUNCH(name, st, (k_ulv_wide<CONJ><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+        // columns per CTA to suit k; inner-index slices until the grid covers two waves of SMs
+        const int CB = wide_cb(k);
+        const int rb = cdiv(m, kWideRows), cbn = cdiv(k, CB);
+        const int nsplit = wide_nsplit(m, k, nodes, nsms);
+        const int jslice = kWideJ * cdiv(cdiv(m, nsplit), kWideJ);
+        const dim3 g(nodes, cbn * nsplit, rb);
+        if (CB == 16)
+            FIO_LAUNCH(name, st, (k_ulv_wide<CONJ, 16><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k, nsplit, jslice, part)));
+        else if (CB == 32)
+            FIO_LAUNCH(name, st, (k_ulv_wide<CONJ, 32><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k, nsplit, jslice, part)));
+        else
+            FIO_LAUNCH(name, st, (k_ulv_wide<CONJ, 64><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k, nsplit, jslice, part)));
+        if (nsplit > 1) {
+            const int64_t per = int64_t(k) * nodes * m;
+            FIO_LAUNCH("k_ulv_reduce", st, (k_ulv_wide_reduce<<<cdiv(per, 256), 256, 0, st>>>(part, nsplit, nodes, m, k, outC, nC, ldC, outD, ldD)));
+        }
     } else {
         const dim3 g(nodes, (k + KCOL - 1) / KCOL, (m + RB - 1) / RB);
         FIO_LAUNCH(name, st, (k_ulv_node_gemm<CONJ><<<g, 256, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
@@ -707,6 +760,17 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
     auto cv = [&](int l) { return w + oc[l] * k; };
     const float2* B = static_cast<const float2*>(Bv);
     float2* X = static_cast<float2*>(Xv);
+    int dev = 0, nsms = 148;
+    FIO_CUDA(cudaGetDevice(&dev));
+    FIO_CUDA(cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t part_need = 1;
+    if (k > kSkinnyMaxK)
+        for (int l = 1; l <= Lh; ++l) {
+            const int m = h->m(l);
+            if (m >= 32) part_need = std::max<int64_t>(part_need, int64_t(wide_nsplit(m, k, 1 << l, nsms)) * k * (int64_t(1) << l) * m);
+        }
+    FIO_TRY(h->solve_part.ensure(size_t(part_need) * 8));
+    float2* part = h->solve_part.as<float2>();
     // few columns: the small upper levels (m_l <= 64) and the root run in one single-CTA launch
     const int m0 = 2 * h->ranks[1];
     int lu = 0;
@@ -727,7 +791,7 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
         int64_t nb = (int64_t(1) << l) * (m - r);
         FIO_TRY(node_products<false>("k_ulv_up", h->W[l].as<float2>(), m, in, m, ldin, in, ldin, bh(l), m - r,
                                      std::max<int64_t>(nb, 1), yv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), k,
-                                     1 << l, st));
+                                     1 << l, part, nsms, st));
     }
     if (lu > 0) {
         UpperArgs ua{};
@@ -760,7 +824,7 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
         int64_t nb = (int64_t(1) << l) * (m - r);
         FIO_TRY(node_products<true>("k_ulv_down", h->W[l].as<float2>(), m, bh(l), m - r, std::max<int64_t>(nb, 1),
                                     cv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), out, m, ldo, out, ldo, k, 1 << l,
-                                    st));
+                                    part, nsms, st));
     }
     FIO_CUDA(cudaGetLastError());
     return FIO_OK;

@@ -52,14 +52,16 @@ def test_ulv_solve_matches_oracle(N, leaf, ranks):
 
 
 SOLVE_SHAPES = [(2048, 128, [0, 4, 6, 8, 10]),              # upper levels m = 12..20: one fused launch
-                (4096, 64, [0, 20, 24, 40, 36, 30, 20])]      # m = 48, 80, 72, 60, 40 and leaves of 64
+                (4096, 64, [0, 20, 24, 40, 36, 30, 20]),      # m = 48, 80, 72, 60, 40 and leaves of 64
+                (1024, 256, [0, 200, 150])]                   # m = 300, 256 on 2 and 4 nodes: sliced inner index
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 9, 16, 64, 67])
 @pytest.mark.parametrize("shape", range(len(SOLVE_SHAPES)))
 def test_ulv_solve_every_width(shape, k):
     """Each solve kernel: k <= 8 skinny node products plus the fused upper levels and root
-    (m_l <= 64), k > 8 the wide products (m >= 32) or the tiled ones (m < 32); ragged k."""
+    (m_l <= 64), k > 8 the wide products (m >= 32; few nodes of large m: inner index cut into
+    slices summed by a second kernel) or the tiled ones (m < 32); ragged k."""
     N, leaf, ranks = SOLVE_SHAPES[shape]
     h = random_hss(N, leaf, ranks, np.random.default_rng(N + k))
     g = gpu_hss_from_oracle(h).factor()
