@@ -40,10 +40,13 @@ class FIOSolver2D:
         self.stats = {}
         N = n * n
 
-        def apply_H(X):   # P K~^* K~ P^T X
-            Y = np.empty_like(X)
-            Y[self.perm] = X
-            return self.bf.adjoint(self.bf.apply(Y))[self.perm]
+        def apply_H(X):   # P K~^* K~ P^T X, 64 columns at a time (bounded coefficient states)
+            out = np.empty_like(X)
+            for c0 in range(0, X.shape[1], 64):
+                Y = np.empty_like(X[:, c0:c0 + 64])
+                Y[self.perm] = X[:, c0:c0 + 64]
+                out[:, c0:c0 + 64] = self.bf.adjoint(self.bf.apply(Y))[self.perm]
+            return out
 
         self.hss = build_blackbox(apply_H, N, leaf, p, tol, seed, rank_frac=rank_frac, stats=self.stats)
         self.ulv = ULV(self.hss)
