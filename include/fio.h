@@ -268,9 +268,24 @@ fio_status hss_matvec(const fio_hss* hss, const void* X, void* Y, int64_t ld, in
  *   Errors: FIO_ENOTHPD (a pivot <= 0), FIO_ENOMEM, FIO_ECUDA. */
 fio_status hss_ulv_factor(fio_hss* hss, void* stream);
 
-/* hss_solve -- X = G~^{-1} B by the ULV bottom-up / root / top-down passes.
- *   B, X: device, N x k complex64, ld >= N; B may equal X. */
+/* hss_solve -- X = G~^{-1} B by the ULV bottom-up / root / top-down passes
+ *   (Section 2.4).  B, X: device, N x k complex64, ld >= N; B may equal X.
+ *   Per level the node products W_t y_t (up) and W_t^* c_t (down) run as:
+ *   k <= 8: one row per thread streaming W (the small upper levels and the
+ *   root in one launch); k > 8: register-tiled CUDA-core FP32 products, or
+ *   with solve path 1 (hss_set_solve_path) and 32 <= m_l <= 512 on the tensor
+ *   cores (tcgen05, FP16 hi/lo parts with power-of-two row and column scales,
+ *   FP32 accumulation: FP32 accuracy; BF16 parts when fio_solve runs on a
+ *   split-precision BF handle).  A bounded MMA wait that runs out is reported
+ *   by fio_device_status.
+ *   Errors: FIO_EINVAL (not factored, k < 0, ld < N), FIO_ENOMEM, FIO_ECUDA. */
 fio_status hss_solve(const fio_hss* hss, const void* B, void* X, int64_t ld, int k, void* stream);
+
+/* hss_set_solve_path -- 0 (default): node products on the CUDA cores in FP32;
+ *   1: the tensor-core node products where they apply (see hss_solve; split
+ *   precision of Section 5's mixed-precision setting for the HSS products).
+ *   Errors: FIO_EINVAL (null handle, path not 0 or 1). */
+fio_status hss_set_solve_path(fio_hss* hss, int path);
 
 /* fio_solve -- online stage f = G~^{-1} K~^* u (Eq. 4.2), plus `refine_steps`
  *   steps of iterative refinement f += G~^{-1}(K~^* u - K~^* K~ f) whose
@@ -364,7 +379,8 @@ fio_status fio_batch_autotune(fio_batch* batch, const void* const* U, void* cons
 void fio_batch_free(fio_batch* batch);
 
 /* fio_device_status -- FIO_ETIMEOUT if a bounded wait inside a tensor-core
- *   kernel (an mbarrier wait for its MMAs) ran out since the last call, which
+ *   kernel (an mbarrier wait for its MMAs: BF half passes or ULV node products)
+ *   ran out since the last call, which
  *   marks that launch's results invalid; the flag is cleared.  Synchronizes
  *   with the device (reads a device flag).  No paper counterpart. */
 fio_status fio_device_status(void);

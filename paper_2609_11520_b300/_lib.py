@@ -64,6 +64,7 @@ SIGNATURES = {
     "hss_matvec": (I32, [P, P, P, I64, I32, P]),
     "hss_ulv_factor": (I32, [P, P]),
     "hss_solve": (I32, [P, P, P, I64, I32, P]),
+    "hss_set_solve_path": (I32, [P, I32]),
     "fio_solve": (I32, [P, P, P, P, I64, I32, I32, P]),
     "hss_free": (None, [P]),
     "fio_batch_create": (I32, [ctypes.POINTER(P), ctypes.POINTER(P), I32, PP]),

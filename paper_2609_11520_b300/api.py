@@ -239,6 +239,12 @@ class HSS:
         self.factored = True
         return self
 
+    def set_solve_path(self, path):
+        """"cuda_cores" (default) or "tensor_cores" (node products of k > 8 columns on tcgen05 with
+        FP16 or, under a split-precision BF handle, BF16 parts; hss_set_solve_path)."""
+        check(lib.hss_set_solve_path(self._h, int({"cuda_cores": 0, "tensor_cores": 1}.get(path, path))))
+        return self
+
     def solve(self, Bm, out=None, stream=None):
         px, ld, k = _block(Bm, self.n, "B")
         out = torch.empty_like(Bm) if out is None else out

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "bf.cuh"
+#include "hss.cuh"
 
 namespace fio {
 namespace {
@@ -843,8 +844,9 @@ extern "C" fio_status bf_set_path(fio_bf* bf, int path) {
 }
 
 extern "C" fio_status fio_device_status(void) {
-    const int v = tc_wait_timeouts();
-    if (v < 0) return fail(FIO_ECUDA, "fio_device_status: reading the device flag failed");
+    const int v1 = tc_wait_timeouts(), v2 = ulv_tc_timeouts();
+    if (v1 < 0 || v2 < 0) return fail(FIO_ECUDA, "fio_device_status: reading the device flag failed");
+    const int v = v1 | v2;
     if (v > 0) return fail(FIO_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (results of that launch are invalid)");
     return FIO_OK;
 }

@@ -49,7 +49,8 @@ extern "C" fio_status fio_solve(const fio_bf* bf, const fio_hss* hc, const void*
     if (mort) F = T + size_t(nbuf - 1) * ld * k;               // solution in Morton order
     const float2* Uc = static_cast<const float2*>(U);
     FIO_TRY(bf_apply_ord(bf, Uc, T, ld, k, 1, mort, st));      // T = K~^* u
-    FIO_TRY(hss_solve(h, T, F, ld, k, st));                    // f = G~^{-1} T
+    const int hp = bf->split ? 1 : 0;                          // node products in the handle's precision
+    FIO_TRY(hss_solve_prec(h, T, F, ld, k, hp, st));           // f = G~^{-1} T
     if (refine_steps > 0) {
         float2* R1 = T + ld * k;
         float2* R2 = R1 + ld * k;
@@ -67,7 +68,7 @@ extern "C" fio_status fio_solve(const fio_bf* bf, const fio_hss* hc, const void*
             if (s == FIO_OK) s = bf_apply_ord(bf, R1, R2, ld, k, 1, mort, st, 0);             // K~^* K~ f
             if (s != FIO_OK) break;
             FIO_LAUNCH("k_sub", st, k_sub<<<g, 256, 0, st>>>(T32, R2, R1, N, ld, ld, ld));
-            s = hss_solve(h, R1, R2, ld, k, st);
+            s = hss_solve_prec(h, R1, R2, ld, k, hp, st);
             if (s == FIO_OK) FIO_LAUNCH("k_add", st, k_add<<<g, 256, 0, st>>>(static_cast<float2*>(F), R2, N, ld, ld));
         }
         FIO_TRY(s);

@@ -864,6 +864,7 @@ extern "C" void hss_free(fio_hss* h) {
     for (auto& b : h->U) b.release();
     for (auto& b : h->B) b.release();
     for (auto& b : h->W) b.release();
+    for (auto& b : h->Wmx) b.release();
     h->D.release();
     h->Rinv.release();
     h->solve_ws.release();

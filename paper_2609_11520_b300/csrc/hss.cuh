@@ -14,9 +14,11 @@ struct fio_hss {
     // ULV factors: W[l] (2^l blocks m_l x m_l, complex64), root inverse
     bool factored = false;
     std::vector<fio::DevBuf> W;
+    std::vector<fio::DevBuf> Wmx;    // per level (32 <= m_l <= 512): largest |Re|, |Im| of each row of W_t, then of W_t^*
     fio::DevBuf Rinv;                // m_0 x m_0 (complex64)
     fio::DevBuf solve_ws;            // per-level vectors of the solve
     fio::DevBuf solve_part;          // partial products of the sliced wide node products
+    int solve_path = 0;              // 0: node products on the CUDA cores; 1: tensor cores where they apply
     fio::DevBuf mv_ws;               // per-level vectors of the matvec
     fio::DevBuf fio_ws;              // K~^* u and refinement vectors of fio_solve
     int64_t samples = 0;
@@ -26,6 +28,10 @@ struct fio_hss {
 };
 
 namespace fio {
+// hss_solve with the precision of the tensor-core node products (0: FP16 parts, 1: BF16 parts).
+fio_status hss_solve_prec(const fio_hss* h, const void* B, void* X, int64_t ld, int k, int prec, cudaStream_t st);
+// Whether a bounded wait of a tensor-core ULV kernel ran out since the last call (cleared); -1 on error.
+int ulv_tc_timeouts();
 // Large nodes (dense64.cu): levels with at most 16 nodes of size m >= the
 // threshold (default 384, fio_set_large_node) run level-3 formulations in mixed
 // precision: FP32 bulk products of the node pass, postprocessing and ULV when the

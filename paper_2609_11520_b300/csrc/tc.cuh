@@ -16,10 +16,48 @@
 // A warp reaches the TMEM lanes 32 * (warp % 4) .. + 31.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace fio {
 namespace tc {
+
+// 16-bit operand parts: v = hi + lo with hi, lo FP16 (BF = false) or BF16 (BF = true).
+template <bool BF> struct Half16;
+template <> struct Half16<false> {
+    using T2 = __half2;
+    static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+    static __device__ __forceinline__ float2 unpack(T2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ uint16_t one(float a) { return __half_as_ushort(__float2half_rn(a)); }
+    static __device__ __forceinline__ float back(uint16_t v) { return __half2float(__ushort_as_half(v)); }
+};
+template <> struct Half16<true> {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    static __device__ __forceinline__ float2 unpack(T2 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ uint16_t one(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    static __device__ __forceinline__ float back(uint16_t v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
+};
+
+// hi / lo parts of (a, b) as two packed 16-bit pairs
+template <bool BF> __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    using H = Half16<BF>;
+    const typename H::T2 h = H::pack(a, b);
+    const float2 f = H::unpack(h);
+    const typename H::T2 l = H::pack(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Power-of-two scale sc (and 1 / sc) for the FP16 parts: largest |entry| (bounded by mx) into
+// [2^14, 2^15), so that neither part overflows or loses bits to the FP16 exponent range.
+__device__ __forceinline__ void row_scale(float mx, float& sc, float& isc) {
+    const int ex = int((__float_as_uint(mx) >> 23) & 0xFF);
+    const int se = ex == 0 ? 127 : min(max(268 - ex, 1), 253);
+    sc = __uint_as_float(uint32_t(se) << 23);
+    isc = __uint_as_float(uint32_t(254 - se) << 23);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 

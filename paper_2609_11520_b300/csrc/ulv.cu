@@ -19,6 +19,7 @@
 
 #include "cplx.cuh"
 #include "hss.cuh"
+#include "tc.cuh"
 #include "ulv_body.cuh"
 
 namespace fio {
@@ -387,8 +388,193 @@ __global__ void k_ulv_wide_reduce(const float2* __restrict__ part, int nsplit, i
     else outD[int64_t(c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = v;
 }
 
+// Tensor-core node products (solve path 1; k > 8, 32 <= m <= 512): Y = op(W_t) X_t as the real product
+//   [Yr | Yi] = [Ar | Ai] [[Xr, Xi], [-Xi, Xr]]     (A = W, or W^* for the down pass)
+// on tcgen05.mma of kind::f16.  Both operands are split into 16-bit parts v = hi + lo and the
+// three products hi hi + hi lo + lo hi accumulate in FP32 in TMEM: FP16 parts with power-of-two
+// scales per row of A and per column of X (FP32 accuracy), or BF16 parts (split precision).
+// CTA: 128 threads, one row of the node's 128-row block per thread (TMEM lane = row), 32 complex
+// columns (N = 64 real); the inner index in chunks of 32 complex (K = 64 real): each thread
+// writes its A row chunk to TMEM (tcgen05.st), the CTA writes the B chunk to shared memory
+// (K-major core matrices), one thread issues 4 x 3 MMAs (M = 128, N = 64, K = 16) and commits
+// them to an mbarrier that every thread waits on with a bounded wait (a run-out sets
+// g_ulv_tc_timeout, read by fio_device_status).
+__device__ int g_ulv_tc_timeout = 0;
+constexpr int kTcCols = 32, kTcJ = 32, kTcTmem = 128, kTcMaxM = 512;
+constexpr uint32_t kTcSbo = (2 * kTcJ / 8) * 128;               // 8-row groups of B (K = 64)
+constexpr int kTcPartBytes = 2 * kTcCols * 2 * kTcJ * 2;        // one 16-bit part of B: 8 KB
+constexpr int kTcSmem = 2 * kTcPartBytes;                       // B_hi | B_lo (the registers allow three CTAs per SM,
+                                                                // within the 4 x 128 TMEM columns)
+__device__ __forceinline__ uint32_t tc_boff(int n, int kk) {    // byte offset of B (n, kk), kk even
+    return uint32_t(n >> 3) * kTcSbo + uint32_t(kk >> 3) * 128 + uint32_t(n & 7) * 16 + uint32_t(kk & 7) * 2;
+}
+template <bool CONJ, bool BF>
+__global__ void __launch_bounds__(128) k_ulv_tc(const float2* __restrict__ W, const float* __restrict__ Wmx, int m,
+                                                const float2* __restrict__ inA, int nA, int64_t ldA,
+                                                const float2* __restrict__ inB, int64_t ldB, float2* __restrict__ outC,
+                                                int nC, int64_t ldC, float2* __restrict__ outD, int64_t ldD, int k) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];    // B_hi | B_lo
+    __shared__ float scol[kTcCols], iscol[kTcCols];
+    __shared__ unsigned smax[kTcCols];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_fail;
+    const int t = blockIdx.x, c0 = blockIdx.y * kTcCols, r0 = blockIdx.z * 128;
+    const int tid = threadIdx.x, i = r0 + tid;
+    const int kc = min(kTcCols, k - c0);
+    const float2* Wt = W + int64_t(t) * m * m;
+    auto wv = [&](int j) -> float2 {   // A(i, j) = op(W_t)(i, j)
+        if (CONJ) {
+            const float2 v = __ldg(Wt + j + int64_t(i) * m);
+            return make_float2(v.x, -v.y);
+        }
+        return __ldg(Wt + i + int64_t(j) * m);
+    };
+    auto xv = [&](int j, int c) -> float2 {
+        return (j < nA) ? inA[int64_t(c0 + c) * ldA + int64_t(t) * nA + j]
+                        : inB[int64_t(c0 + c) * ldB + int64_t(t) * (m - nA) + (j - nA)];
+    };
+    if (tid < 32) tc::tmem_alloc(&s_tmem, kTcTmem);
+    if (tid == 0) {
+        tc::mbar_init(&s_mbar, 1);
+        s_fail = 0;
+    }
+    if (tid < kTcCols) smax[tid] = 0u;
+    __syncthreads();
+    float rsc = 1.f, irsc = 1.f;
+    if (!BF) {   // power-of-two scales: per column of X (four threads per column), per row of A
+        const int c = tid & 31;
+        float mx = 0.f;
+        if (c < kc)
+#pragma unroll 8
+            for (int j = tid >> 5; j < m; j += 4) {
+                const float2 v = xv(j, c);
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        atomicMax(&smax[c], __float_as_uint(mx));
+        // row maxima of W_t and W_t^* stored at factorization
+        const float rm = i < m ? Wmx[(CONJ ? int64_t(gridDim.x) * m : 0) + int64_t(t) * m + i] : 0.f;
+        tc::row_scale(rm, rsc, irsc);
+    }
+    __syncthreads();
+    if (tid < kTcCols) {
+        float sc = 1.f, isc = 1.f;
+        if (!BF) tc::row_scale(__uint_as_float(smax[tid]), sc, isc);
+        scol[tid] = sc;
+        iscol[tid] = isc;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t tl = tmem + (uint32_t(tid & 0x60) << 16);    // this warp's TMEM lanes
+    const uint32_t sb = tc::smem_addr(tc_smem);
+    const uint32_t idesc = tc::idesc_f16(BF, 128, 2 * kTcCols);
+    uint32_t phase = 0;
+    for (int j0 = 0, ch = 0; j0 < m; j0 += kTcJ, ++ch) {
+        {   // A chunk of row i: K = 2 (j - j0) + (re, im), hi in TMEM columns 0..31, lo in 32..63
+            uint32_t h0[16], h1[16], l0[16], l1[16];
+#pragma unroll
+            for (int jj = 0; jj < kTcJ; ++jj) {
+                const int j = j0 + jj;
+                float2 v = make_float2(0.f, 0.f);
+                if (i < m && j < m) v = wv(j);
+                uint32_t h, l;
+                tc::split_pair<BF>(v.x * rsc, v.y * rsc, h, l);
+                if (jj < 16) {
+                    h0[jj] = h;
+                    l0[jj] = l;
+                } else {
+                    h1[jj - 16] = h;
+                    l1[jj - 16] = l;
+                }
+            }
+            tc::tmem_st16(tl + 0, h0);
+            tc::tmem_st16(tl + 16, h1);
+            tc::tmem_st16(tl + 32, l0);
+            tc::tmem_st16(tl + 48, l1);
+        }
+        // B chunk: row n < 32 -> Yr of column n: (Xr, -Xi); n >= 32 -> Yi of column n - 32: (Xi, Xr)
+#pragma unroll
+        for (int e = tid; e < kTcCols * kTcJ; e += 128) {
+            const int jj = e % kTcJ, c = e / kTcJ, j = j0 + jj;
+            float2 x = make_float2(0.f, 0.f);
+            if (c < kc && j < m) x = xv(j, c);
+            const float sc = scol[c];
+            uint32_t h, l;
+            tc::split_pair<BF>(x.x * sc, -x.y * sc, h, l);
+            *reinterpret_cast<uint32_t*>(tc_smem + tc_boff(c, 2 * jj)) = h;
+            *reinterpret_cast<uint32_t*>(tc_smem + kTcPartBytes + tc_boff(c, 2 * jj)) = l;
+            tc::split_pair<BF>(x.y * sc, x.x * sc, h, l);
+            *reinterpret_cast<uint32_t*>(tc_smem + tc_boff(c + kTcCols, 2 * jj)) = h;
+            *reinterpret_cast<uint32_t*>(tc_smem + kTcPartBytes + tc_boff(c + kTcCols, 2 * jj)) = l;
+        }
+        tc::tmem_wait_st();
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0 && !s_fail) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t bh = tc::smem_desc(sb + 256 * ks, 128, kTcSbo);
+                const uint64_t bl = tc::smem_desc(sb + kTcPartBytes + 256 * ks, 128, kTcSbo);
+                tc::mma_f16_ts(tmem + 64, tmem + 8 * ks, bh, idesc, (ch > 0 || ks > 0) ? 1 : 0);
+                tc::mma_f16_ts(tmem + 64, tmem + 8 * ks, bl, idesc, 1);
+                tc::mma_f16_ts(tmem + 64, tmem + 32 + 8 * ks, bh, idesc, 1);
+            }
+            tc::mma_commit(&s_mbar);
+        }
+        if (!s_fail && !tc::mbar_wait(&s_mbar, phase)) {
+            s_fail = 1;
+            atomicExch(&g_ulv_tc_timeout, 1);
+        }
+        phase ^= 1u;
+        tc::fence_after();
+        __syncthreads();   // every thread past the wait before the next chunk overwrites A and B
+    }
+    uint32_t d0[16], d1[16], d2[16], d3[16];   // D columns 0..31 (Yr), 32..63 (Yi)
+    tc::tmem_ld16(tl + 64, d0);
+    tc::tmem_ld16(tl + 80, d1);
+    tc::tmem_ld16(tl + 96, d2);
+    tc::tmem_ld16(tl + 112, d3);
+    tc::tmem_wait_ld();
+    if (i < m && !s_fail) {
+#pragma unroll
+        for (int c = 0; c < kTcCols; ++c) {
+            if (c >= kc) break;
+            const float re = __uint_as_float(c < 16 ? d0[c] : d1[c - 16]);
+            const float im = __uint_as_float(c < 16 ? d2[c] : d3[c - 16]);
+            const float sc = irsc * iscol[c];
+            const float2 y = make_float2(re * sc, im * sc);
+            if (i < nC) outC[int64_t(c0 + c) * ldC + int64_t(t) * nC + i] = y;
+            else outD[int64_t(c0 + c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = y;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid < 32) tc::tmem_free(tmem, kTcTmem);
+}
+
+// Row maxima of the node matrices for the FP16 scales of k_ulv_tc: out[t m + i] = largest |Re|,
+// |Im| of row i of W_t; out[nodes m + t m + i] = the same of row i of W_t^* (column i of W_t).
+__global__ void k_ulv_rowmax(const float2* __restrict__ W, int m, int nodes, float* __restrict__ out) {
+    const int t = blockIdx.x, i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float2* Wt = W + int64_t(t) * m * m;
+    float up = 0.f, dn = 0.f;
+    for (int j = 0; j < m; ++j) {
+        const float2 a = Wt[i + int64_t(j) * m], b = Wt[j + int64_t(i) * m];
+        up = fmaxf(up, fmaxf(fabsf(a.x), fabsf(a.y)));
+        dn = fmaxf(dn, fmaxf(fabsf(b.x), fabsf(b.y)));
+    }
+    out[int64_t(t) * m + i] = up;
+    out[int64_t(nodes) * m + int64_t(t) * m + i] = dn;
+}
+
 // Skinny node products (k <= KC <= 8 columns): one CTA of 128 threads per (node, 128 rows), one
-// output row per thread; W streamed from HBM once with eight loads in flight per thread (up pass:
+// output row per thread; W streamed from HBM once with sixteen loads in flight per thread (up pass:
 // coalesced column segments; down pass: each thread's own contiguous column of W, i.e. a row of
 // W^*); x staged through shared memory in tiles of 512 inner indices.
 constexpr int kSkinnyJ = 512;
@@ -418,7 +604,7 @@ __global__ void __launch_bounds__(128) k_ulv_skinny(const float2* __restrict__ W
         if (i < m) {
             if (!CONJ) {
                 const float2* wp = Wt + i + int64_t(j0) * m;
-#pragma unroll 8
+#pragma unroll 16
                 for (int jj = 0; jj < jw; ++jj) {
                     const float2 w = __ldg(wp + int64_t(jj) * m);
 #pragma unroll
@@ -426,7 +612,7 @@ __global__ void __launch_bounds__(128) k_ulv_skinny(const float2* __restrict__ W
                 }
             } else {
                 const float2* wp = Wt + int64_t(i) * m + j0;
-#pragma unroll 8
+#pragma unroll 16
                 for (int jj = 0; jj < jw; ++jj) {
                     const float2 w = __ldg(wp + jj);
 #pragma unroll
@@ -521,14 +707,21 @@ int wide_nsplit(int m, int k, int nodes, int nsms) {
     return cdiv(m, jslice);
 }
 
-// The node products of one solve level with the kernel that suits k: skinny (k <= 8), wide
-// (m >= 32), else the tiled k_ulv_node_gemm.
+// The node products of one solve level with the kernel that suits k: skinny (k <= 8), tensor
+// cores (tc: 1 FP16 parts, 2 BF16 parts; 32 <= m <= 512), wide CUDA-core products (m >= 32),
+// else the tiled k_ulv_node_gemm.
 // part: scratch of at least wide_nsplit(m, k, nodes, nsms) * k * nodes * m complex.
 template <bool CONJ>
-fio_status node_products(const char* name, const float2* W, int m, const float2* inA, int nA, int64_t ldA,
-                         const float2* inB, int64_t ldB, float2* outC, int nC, int64_t ldC, float2* outD, int64_t ldD,
-                         int k, int nodes, float2* part, int nsms, cudaStream_t st) {
-    if (k <= kSkinnyMaxK) {
+fio_status node_products(const char* name, const float2* W, const float* Wmx, int m, const float2* inA, int nA,
+                         int64_t ldA, const float2* inB, int64_t ldB, float2* outC, int nC, int64_t ldC, float2* outD,
+                         int64_t ldD, int k, int nodes, float2* part, int nsms, int tc, cudaStream_t st) {
+    if (k > kSkinnyMaxK && tc && Wmx && m >= 32 && m <= kTcMaxM) {
+        const dim3 g(nodes, cdiv(k, kTcCols), cdiv(m, 128));
+        if (tc == 2)
+            FIO_LAUNCH(name, st, (k_ulv_tc<CONJ, true><<<g, 128, kTcSmem, st>>>(W, Wmx, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+        else
+            FIO_LAUNCH(name, st, (k_ulv_tc<CONJ, false><<<g, 128, kTcSmem, st>>>(W, Wmx, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+    } else if (k <= kSkinnyMaxK) {
         const dim3 g(nodes, cdiv(m, 128));
         if (k == 1)
             FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 1><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
@@ -730,17 +923,42 @@ extern "C" fio_status hss_ulv_factor(fio_hss* h, void* stream) {
     release();
     if (e != cudaSuccess) return cuda_status(e, "hss_ulv_factor");
     if (hst == FIO_ENOTHPD) return fail(FIO_ENOTHPD, "hss_ulv_factor: Cholesky pivot <= 0 (G~ not HPD)");
+    // row maxima of the node matrices of the tensor-core solve levels
+    h->Wmx.resize(Lh + 1);
+    for (int l = 1; l <= Lh; ++l) {
+        const int m = h->m(l), nn = 1 << l;
+        if (m < 32 || m > kTcMaxM) continue;
+        if ((s = h->Wmx[l].ensure(size_t(2) * nn * m * sizeof(float))) != FIO_OK) return s;
+        k_ulv_rowmax<<<dim3(nn, cdiv(m, 128)), 128, 0, st>>>(h->W[l].as<float2>(), m, nn, h->Wmx[l].as<float>());
+    }
+    FIO_CUDA(cudaGetLastError());
+    FIO_CUDA(cudaStreamSynchronize(st));
     h->factored = true;
     return FIO_OK;
 }
 
-extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int64_t ld, int k, void* stream) {
+namespace fio {
+// hss_solve with the precision of the tensor-core node products (prec 0: FP16 parts, FP32
+// accuracy; 1: BF16 parts), used when the handle's solve path is 1; path 0 (default) runs every
+// node product on the CUDA cores in FP32.
+fio_status hss_solve_prec(const fio_hss* hc, const void* Bv, void* Xv, int64_t ld, int k, int prec, cudaStream_t st) {
     if (!hc) return fail(FIO_EINVAL, "hss_solve: null handle");
     if (!hc->factored) return fail(FIO_EINVAL, "hss_solve: call hss_ulv_factor first");
     if (k < 0 || ld < hc->N) return fail(FIO_EINVAL, "hss_solve: need k >= 0 and ld >= N");
     if (k == 0) return FIO_OK;
     fio_hss* h = const_cast<fio_hss*>(hc);
-    cudaStream_t st = as_stream(stream);
+    const int tc = hc->solve_path == 1 ? (prec == 1 ? 2 : 1) : 0;
+    auto wmx = [&](int l) -> const float* {
+        return (l < int(h->Wmx.size()) && h->Wmx[l].p) ? h->Wmx[l].as<float>() : nullptr;
+    };
+    static PerDeviceOnce attrs;
+    FIO_CUDA(attrs.run([] {
+        cudaError_t e = cudaSuccess;
+        for (auto f : {(const void*)k_ulv_tc<false, false>, (const void*)k_ulv_tc<true, false>,
+                       (const void*)k_ulv_tc<false, true>, (const void*)k_ulv_tc<true, true>})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        return e;
+    }));
     const int Lh = h->Lh;
     // per level: bh1_l (2^l (m_l - r_l)), y_l (rows(l), l < Lh), c_l (rows(l), l < Lh)
     std::vector<int64_t> ob(Lh + 1), oy(Lh + 1), oc(Lh + 1);
@@ -789,9 +1007,9 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
         const float2* in = (l == Lh) ? B : yv(l);
         int64_t ldin = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        FIO_TRY(node_products<false>("k_ulv_up", h->W[l].as<float2>(), m, in, m, ldin, in, ldin, bh(l), m - r,
+        FIO_TRY(node_products<false>("k_ulv_up", h->W[l].as<float2>(), wmx(l), m, in, m, ldin, in, ldin, bh(l), m - r,
                                      std::max<int64_t>(nb, 1), yv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), k,
-                                     1 << l, part, nsms, st));
+                                     1 << l, part, nsms, tc, st));
     }
     if (lu > 0) {
         UpperArgs ua{};
@@ -822,11 +1040,30 @@ extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int
         float2* out = (l == Lh) ? X : cv(l);
         int64_t ldo = (l == Lh) ? ld : h->rows(l);
         int64_t nb = (int64_t(1) << l) * (m - r);
-        FIO_TRY(node_products<true>("k_ulv_down", h->W[l].as<float2>(), m, bh(l), m - r, std::max<int64_t>(nb, 1),
+        FIO_TRY(node_products<true>("k_ulv_down", h->W[l].as<float2>(), wmx(l), m, bh(l), m - r, std::max<int64_t>(nb, 1),
                                     cv(l - 1), std::max<int64_t>(h->rows(l - 1), 1), out, m, ldo, out, ldo, k, 1 << l,
-                                    part, nsms, st));
+                                    part, nsms, tc, st));
     }
     FIO_CUDA(cudaGetLastError());
+    return FIO_OK;
+}
+
+int ulv_tc_timeouts() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_ulv_tc_timeout, sizeof(int)) != cudaSuccess) return -1;
+    const int z = 0;
+    if (v) cudaMemcpyToSymbol(g_ulv_tc_timeout, &z, sizeof(int));
+    return v;
+}
+}  // namespace fio
+
+extern "C" fio_status hss_solve(const fio_hss* hc, const void* Bv, void* Xv, int64_t ld, int k, void* stream) {
+    return hss_solve_prec(hc, Bv, Xv, ld, k, 0, as_stream(stream));
+}
+
+extern "C" fio_status hss_set_solve_path(fio_hss* h, int path) {
+    if (!h || path < 0 || path > 1) return fail(FIO_EINVAL, "hss_set_solve_path: bad handle or path");
+    h->solve_path = path;
     return FIO_OK;
 }
 

@@ -69,6 +69,23 @@ def test_ulv_solve_every_width(shape, k):
     assert rel(to_np(g.solve(to_dev(Y))), ULV(h).solve(Y)) < 1e-4
 
 
+@pytest.mark.parametrize("k", [9, 32, 64, 67])
+@pytest.mark.parametrize("shape", [1, 2])
+def test_ulv_tensor_core_products_match_cuda_cores(shape, k):
+    """k > 8: the tcgen05 node products (FP16 hi/lo parts, power-of-two scales) against the FP32
+    CUDA-core products on the same factorization.  Each part product is exact to 2^-22 of its
+    row/column scale and an output sums K = 2 m_l (up to 600) of them, so the two paths differ
+    by about sqrt(K) 2^-22 ~ 6e-6 relative: bound 2e-5.  Parity with the oracle stays 1e-4."""
+    N, leaf, ranks = SOLVE_SHAPES[shape]
+    h = random_hss(N, leaf, ranks, np.random.default_rng(7 * N + k))
+    g = gpu_hss_from_oracle(h).factor()
+    Y = to_dev(crandn(N, k, seed=100 + k))
+    b = to_np(g.solve(Y))
+    a = to_np(g.set_solve_path("tensor_cores").solve(Y))
+    assert rel(a, b) < 2e-5
+    assert rel(a, ULV(h).solve(to_np(Y))) < 1e-4
+
+
 def test_ulv_rejects_indefinite():
     from paper_2609_11520_b300 import FioError
     h = random_hss(128, 32, [0, 4, 4], np.random.default_rng(3), shift=0.0)

@@ -78,3 +78,27 @@ def test_split_solve_and_refinement():
     assert abs(e_split - e32) < 0.1 * e32
     assert e_ref < 0.1 * e_split, (e_ref, e_split)
     assert e_ref2 <= e_ref * 1.01 + 1e-6
+
+
+@pytest.mark.parametrize("k", [16, 40])
+def test_split_solve_with_tensor_core_hss_products(k):
+    """Split precision on the HSS products too: the ULV node products of k > 8 columns on the
+    tensor cores with BF16 hi/lo parts (solve path 1 under a split-precision BF handle).  The
+    solve error stays within 2x the oracle's (the HSS tolerance dominates BF16 hi/lo rounding) and
+    one FP32-residual refinement step still gains an order of magnitude."""
+    from paper_2609_11520_b300 import BF, HSS, fio_solve
+    n, leaf, p, tol, seed = 4096, 128, 10, 1e-3, 1
+    S = FIOSolver(Phase("cabs"), n, 16, leaf, p, tol, seed)
+    f = crandn(n, k, seed=3)
+    u = S.bf.apply(f)
+    e_oracle = rel(S.solve(u), f)
+    bf = BF(n, 16).set_precision("split_bf16")
+    g = HSS.from_samples(bf=bf, leaf=leaf, oversample=p, tol=tol, seed=seed).factor()
+    U = to_dev(u)
+    e_cc = rel(to_np(fio_solve(bf, g, U)), f)
+    g.set_solve_path("tensor_cores")
+    e_tc = rel(to_np(fio_solve(bf, g, U)), f)
+    e_ref = rel(to_np(fio_solve(bf, g, U, refine_steps=1)), f)
+    assert e_tc <= 2 * e_oracle, (e_tc, e_oracle)
+    assert abs(e_tc - e_cc) < 0.1 * e_cc
+    assert e_ref < 0.1 * e_tc, (e_ref, e_tc)
