@@ -824,11 +824,17 @@ def main():
         e_sp = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
         sp1 = timed(lambda: fio_solve(bf, hss, U, out=OUT, refine_steps=1), args.steps, args.warmup)
         e_sp1 = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+        # split precision on the HSS products too: the ULV node products on the tensor cores (BF16 parts)
+        hss.set_solve_path("tensor_cores")
+        sph = timed(lambda: fio_solve(bf, hss, U, out=OUT), args.steps, args.warmup)
+        e_sph = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
+        hss.set_solve_path("cuda_cores")
         bf.set_precision("fp32")
         fp1 = timed(lambda: fio_solve(bf, hss, U, out=OUT, refine_steps=1), args.steps, args.warmup)
         e_fp1 = float(torch.linalg.norm(OUT - F_true) / torch.linalg.norm(F_true))
         split = {"value": world * k * args.steps / (sum(sp) / 1e3), "unit": UNIT, "e_direct_vs_f_true": e_sp,
                  "refine1": {"value": world * k * args.steps / (sum(sp1) / 1e3), "e_vs_f_true": e_sp1},
+                 "hss_tensor_cores": {"value": world * k * args.steps / (sum(sph) / 1e3), "e_direct_vs_f_true": e_sph},
                  "fp32_refine1": {"value": world * k * args.steps / (sum(fp1) / 1e3), "e_vs_f_true": e_fp1}}
 
     # ---- preconditioned CG on Eq. 4.3 (Section 4.1), same block, tolerance 1e-5 ----
