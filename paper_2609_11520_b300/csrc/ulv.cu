@@ -573,18 +573,21 @@ __global__ void k_ulv_rowmax(const float2* __restrict__ W, int m, int nodes, flo
     out[int64_t(nodes) * m + int64_t(t) * m + i] = dn;
 }
 
-// Skinny node products (k <= KC <= 8 columns): one CTA of 128 threads per (node, 128 rows), one
-// output row per thread; W streamed from HBM once with sixteen loads in flight per thread (up pass:
-// coalesced column segments; down pass: each thread's own contiguous column of W, i.e. a row of
-// W^*); x staged through shared memory in tiles of 512 inner indices.
-constexpr int kSkinnyJ = 512;
+// Skinny node products (k <= KC <= 8 columns): one CTA of 4 x 128 threads per (node, 128 rows);
+// thread (group g, row) sums over the g-th quarter of each tile of inner indices, and the four
+// partial sums meet in shared memory at the end.  W is streamed from HBM once (up pass: coalesced
+// column segments; down pass: each thread's own contiguous column of W, i.e. a row of W^*); x is
+// staged through shared memory in tiles of 512 inner indices.
+constexpr int kSkinnyJ = 512, kSkinnyG = 4;
 template <bool CONJ, int KC>
-__global__ void __launch_bounds__(128) k_ulv_skinny(const float2* __restrict__ W, int m, const float2* __restrict__ inA,
-                                                    int nA, int64_t ldA, const float2* __restrict__ inB, int64_t ldB,
-                                                    float2* __restrict__ outC, int nC, int64_t ldC,
-                                                    float2* __restrict__ outD, int64_t ldD, int k) {
-    __shared__ float2 sx[kSkinnyJ][KC];
-    const int t = blockIdx.x, il = threadIdx.x, i = blockIdx.y * 128 + il;
+__global__ void __launch_bounds__(128 * kSkinnyG) k_ulv_skinny(const float2* __restrict__ W, int m,
+                                                               const float2* __restrict__ inA, int nA, int64_t ldA,
+                                                               const float2* __restrict__ inB, int64_t ldB,
+                                                               float2* __restrict__ outC, int nC, int64_t ldC,
+                                                               float2* __restrict__ outD, int64_t ldD, int k) {
+    __shared__ float2 sx[kSkinnyJ * KC];   // x tile [jj][c]; at the end the partial sums [g][row][c]
+    constexpr int NTH = 128 * kSkinnyG;
+    const int t = blockIdx.x, il = threadIdx.x & 127, g = threadIdx.x >> 7, i = blockIdx.y * 128 + il;
     const float2* Wt = W + int64_t(t) * m * m;
     float2 acc[KC];
 #pragma unroll
@@ -592,41 +595,49 @@ __global__ void __launch_bounds__(128) k_ulv_skinny(const float2* __restrict__ W
     for (int j0 = 0; j0 < m; j0 += kSkinnyJ) {
         const int jw = min(kSkinnyJ, m - j0);
         __syncthreads();
-        for (int e = il; e < kSkinnyJ * KC; e += 128) {
+        for (int e = threadIdx.x; e < kSkinnyJ * KC; e += NTH) {
             const int jj = e % kSkinnyJ, c = e / kSkinnyJ, j = j0 + jj;
             float2 v = make_float2(0.f, 0.f);
             if (jj < jw && c < k)
                 v = (j < nA) ? inA[int64_t(c) * ldA + int64_t(t) * nA + j]
                              : inB[int64_t(c) * ldB + int64_t(t) * (m - nA) + (j - nA)];
-            sx[jj][c] = v;
+            sx[jj * KC + c] = v;
         }
         __syncthreads();
+        const int q = (jw + kSkinnyG - 1) / kSkinnyG, jb = g * q, je = min(jw, jb + q);
         if (i < m) {
             if (!CONJ) {
                 const float2* wp = Wt + i + int64_t(j0) * m;
-#pragma unroll 16
-                for (int jj = 0; jj < jw; ++jj) {
+#pragma unroll 8
+                for (int jj = jb; jj < je; ++jj) {
                     const float2 w = __ldg(wp + int64_t(jj) * m);
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) cfma(acc[c], w, sx[jj][c]);
+                    for (int c = 0; c < KC; ++c) cfma(acc[c], w, sx[jj * KC + c]);
                 }
             } else {
                 const float2* wp = Wt + int64_t(i) * m + j0;
-#pragma unroll 16
-                for (int jj = 0; jj < jw; ++jj) {
+#pragma unroll 8
+                for (int jj = jb; jj < je; ++jj) {
                     const float2 w = __ldg(wp + jj);
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) cfmac(acc[c], w, sx[jj][c]);
+                    for (int c = 0; c < KC; ++c) cfmac(acc[c], w, sx[jj * KC + c]);
                 }
             }
         }
     }
-    if (i >= m) return;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < KC; ++c) sx[(g * 128 + il) * KC + c] = acc[c];
+    __syncthreads();
+    if (g != 0 || i >= m) return;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
         if (c >= k) break;
-        if (i < nC) outC[int64_t(c) * ldC + int64_t(t) * nC + i] = acc[c];
-        else outD[int64_t(c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = acc[c];
+        float2 v = sx[il * KC + c];
+#pragma unroll
+        for (int gg = 1; gg < kSkinnyG; ++gg) v = cadd(v, sx[(gg * 128 + il) * KC + c]);
+        if (i < nC) outC[int64_t(c) * ldC + int64_t(t) * nC + i] = v;
+        else outD[int64_t(c) * ldD + int64_t(t) * (m - nC) + (i - nC)] = v;
     }
 }
 
@@ -724,13 +735,13 @@ fio_status node_products(const char* name, const float2* W, const float* Wmx, in
     } else if (k <= kSkinnyMaxK) {
         const dim3 g(nodes, cdiv(m, 128));
         if (k == 1)
-            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 1><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 1><<<g, 128 * kSkinnyG, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
         else if (k == 2)
-            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 2><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 2><<<g, 128 * kSkinnyG, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
         else if (k <= 4)
-            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 4><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 4><<<g, 128 * kSkinnyG, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
         else
-            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 8><<<g, 128, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
+            FIO_LAUNCH(name, st, (k_ulv_skinny<CONJ, 8><<<g, 128 * kSkinnyG, 0, st>>>(W, m, inA, nA, ldA, inB, ldB, outC, nC, ldC, outD, ldD, k)));
     } else if (m >= 32) {
         // columns per CTA to suit k; inner-index slices until the grid covers two waves of SMs
         const int CB = wide_cb(k);
