@@ -381,6 +381,89 @@ __global__ void __launch_bounds__(TB, R1 <= 5 ? 2 : 1) k2_trans(const float2* __
     for (int v = 0; v < R; ++v) out[v] = acc[v];
 }
 
+// The same transfer level for r1 >= 6: thread (group, column, u) as above, but the R outputs in two
+// halves of VH, one after the other, and the inner index t in blocks of four (one float4 of A per
+// output row per block), so that a thread holds VH (SM) or 2 VH (MS) complex accumulators instead
+// of 2 R values and two CTAs fit on an SM.  The SM form recomputes the phase products per half,
+// the MS form reloads the inputs.
+template <int R1, bool SM, bool ADJ>
+__global__ void __launch_bounds__(TB, 2) k2_trans_h(const float2* __restrict__ Sin, float2* __restrict__ Sout,
+                                                    int64_t SN, const float2* __restrict__ Ph,
+                                                    const float* __restrict__ Am, int L, int s, int kc) {
+    constexpr int R = G2<R1>::R, RP = G2<R1>::RP, VH = (R + 1) / 2;
+    __shared__ __align__(16) float A[4 * R * RP];
+    for (int i = threadIdx.x; i < 4 * R * RP; i += TB) A[i] = Am[i];
+    __syncthreads();
+    const int u = threadIdx.x & 3;
+    const int64_t ngroups = int64_t(1) << (2 * L - 2);
+    const int64_t item = int64_t(blockIdx.x) * (TB / 4) + (threadIdx.x >> 2);
+    if (item >= ngroups * kc) return;
+    const int col = int(item % kc);
+    const int64_t g = item / kc;
+    const int64_t nbq = int64_t(1) << (2 * (L - s - 1));
+    const int64_t tau = g / nbq, sq = g % nbq;
+    auto low = [&](int c) { return tau * (nbq * 4) + child_id(L - s - 1, sq, c); };
+    auto high = [&](int o) { return child_id(s, tau, o) * nbq + sq; };
+    const float2* xin = Sin + col * SN;
+    float2* out = Sout + col * SN + (ADJ ? low(u) : high(u)) * R;
+#pragma unroll 1
+    for (int v0 = 0; v0 < R; v0 += VH) {
+        const int nv = min(VH, R - v0);
+        float2 acc[VH];
+#pragma unroll
+        for (int v = 0; v < VH; ++v) acc[v] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+            const float2* x = xin + (ADJ ? high(w) : low(w)) * R;
+            const int o = ADJ ? w : u, c = ADJ ? u : w;
+            const float2* ph = Ph + ((g * 4 + o) * 4 + c) * R;
+            float2 tmp[SM ? 1 : VH];
+            if (!SM)
+#pragma unroll
+                for (int v = 0; v < VH; ++v) tmp[v] = make_float2(0.f, 0.f);
+            const float* Ab = A + ((SM ? w : u) * R + v0) * RP;   // rows v0 .. v0 + VH - 1
+#pragma unroll 1
+            for (int t0 = 0; t0 < R; t0 += 4) {
+                float2 y[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    const int t = min(t0 + d, R - 1);
+                    const float2 xv = __ldg(x + t);
+                    float2 v = xv;
+                    if (SM) {
+                        const float2 pv = __ldg(ph + t);
+                        v = ADJ ? cmulc(pv, xv) : cmul(pv, xv);
+                    }
+                    y[d] = t0 + d < R ? v : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int v = 0; v < VH; ++v) {
+                    if (v >= nv) break;
+                    const float4 a = *reinterpret_cast<const float4*>(Ab + v * RP + t0);
+                    float2& dst = SM ? acc[v] : tmp[SM ? 0 : v];
+                    dst.x = fmaf(a.x, y[0].x, dst.x); dst.y = fmaf(a.x, y[0].y, dst.y);
+                    dst.x = fmaf(a.y, y[1].x, dst.x); dst.y = fmaf(a.y, y[1].y, dst.y);
+                    dst.x = fmaf(a.z, y[2].x, dst.x); dst.y = fmaf(a.z, y[2].y, dst.y);
+                    dst.x = fmaf(a.w, y[3].x, dst.x); dst.y = fmaf(a.w, y[3].y, dst.y);
+                }
+            }
+            if (!SM)
+#pragma unroll
+                for (int v = 0; v < VH; ++v) {
+                    if (v >= nv) break;
+                    const float2 pv = __ldg(ph + v0 + v);
+                    if (ADJ) cfmac(acc[v], pv, tmp[v]);
+                    else cfma(acc[v], pv, tmp[v]);
+                }
+        }
+#pragma unroll
+        for (int v = 0; v < VH; ++v) {
+            if (v >= nv) break;
+            out[v0 + v] = acc[v];
+        }
+    }
+}
+
 // Middle level: y[i] = sum_j M[p][i][j] x[j] (adjoint: x[j] = sum_i conj(M[p][i][j]) y[i]).
 // CTA: MP pairs x TB / MP columns; thread (pair, column).
 template <int R1, bool ADJ>
@@ -787,13 +870,22 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
     const dim3 gV(unsigned(int64_t(1) << (2 * (L - sV))), cdiv(kc, 4));
     const dim3 gU(unsigned(int64_t(1) << (2 * sU)), cdiv(kc, 4));
     const dim3 gM(cdiv(N, MP), cdiv(kc, TB / MP)), gMq(cdiv(N, G2<R1>::MQP), cdiv(kc, 16));
+    // transfer kernels: all outputs per thread, or for the scale-then-mix form at r1 >= 6 in two
+    // halves (measured at n = 256, r1 = 7: 527 against 487 GB/s; the mix-then-scale form is faster
+    // with all outputs per thread, 509 against 373 GB/s)
+    using TransK = void (*)(const float2*, float2*, int64_t, const float2*, const float*, int, int, int);
+    constexpr bool HALF = G2<R1>::CHUNK_M;
+    const TransK kCf = HALF ? k2_trans_h<R1, true, false> : k2_trans<R1, true, false>;
+    const TransK kBf = k2_trans<R1, false, false>;
+    const TransK kBa = HALF ? k2_trans_h<R1, true, true> : k2_trans<R1, true, true>;
+    const TransK kCa = k2_trans<R1, false, true>;
     float2* cur = s0;
     float2* oth = s1;
     const int m = mort ? 1 : 0;
     if (!adjoint) {
         FIO_LAUNCH("k2_V_fwd", st, k2_V_fwd<R1><<<gV, TB, 0, st>>>(X, ld, cur, SN, bf->VP.as<float2>(), QV, n, L, sV, kc, m));
         for (int s = sV; s < h; ++s) {
-            FIO_LAUNCH("k2_C_fwd", st, (k2_trans<R1, true, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+            FIO_LAUNCH("k2_C_fwd", st, (kCf<<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
                                                                                      Pc, L, s, kc)));
             std::swap(cur, oth);
         }
@@ -803,7 +895,7 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
             FIO_LAUNCH("k2_M_fwd", st, (k2_M<R1, false><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h; s < sU; ++s) {
-            FIO_LAUNCH("k2_B_fwd", st, (k2_trans<R1, false, false><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+            FIO_LAUNCH("k2_B_fwd", st, (kBf<<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
                                                                                       PcT, L, s, kc)));
             std::swap(cur, oth);
         }
@@ -811,7 +903,7 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
     } else {
         FIO_LAUNCH("k2_U_adj", st, k2_U_adj<R1><<<gU, TB, 0, st>>>(X, ld, cur, SN, bf->UP.as<float2>(), QU, n, L, sU, kc));
         for (int s = sU - 1; s >= h; --s) {
-            FIO_LAUNCH("k2_B_adj", st, (k2_trans<R1, true, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
+            FIO_LAUNCH("k2_B_adj", st, (kBa<<<gtr, TB, 0, st>>>(cur, oth, SN, bf->B[s - h].as<float2>(),
                                                                                     Pc, L, s, kc)));
             std::swap(cur, oth);
         }
@@ -821,7 +913,7 @@ fio_status apply2(const fio_bf* bf, const float2* X, float2* Y, int64_t ld, int 
             FIO_LAUNCH("k2_M_adj", st, (k2_M<R1, true><<<gM, TB, sm, st>>>(cur, oth, SN, bf->M.as<float2>(), N, kc)));
         std::swap(cur, oth);
         for (int s = h - 1; s >= sV; --s) {
-            FIO_LAUNCH("k2_C_adj", st, (k2_trans<R1, false, true><<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
+            FIO_LAUNCH("k2_C_adj", st, (kCa<<<gtr, TB, 0, st>>>(cur, oth, SN, bf->C[s - sV].as<float2>(),
                                                                                      PcT, L, s, kc)));
             std::swap(cur, oth);
         }
